@@ -1,0 +1,163 @@
+"""CPU oracle for the exact squared Euclidean distance transform.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use this package; the CUDA library and its Python
+binding never import it.  The arithmetic lives in ``edt_oracle.c`` (plain,
+single-threaded C following Section 3 of T. Strutz, "The Distance Transform
+and its Computation"); this module only compiles it with gcc and marshals
+numpy arrays through ctypes.
+
+Conventions (shared by value, not by code, with the CUDA library):
+  mode 0 = TO_OBJECT      sources are the nonzero mask bytes (Fig. 1c)
+  mode 1 = TO_BACKGROUND  sources are the zero mask bytes (Fig. 1b)
+  D  int32 squared distance, INT32_MAX when the image has no source pixel
+  F  int32 0-based row-major index of a nearest source pixel, -1 without one
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+TO_OBJECT = 0
+TO_BACKGROUND = 1
+INF32 = np.iinfo(np.int32).max
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "edt_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle_edt.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile edt_oracle.c into a shared library (plain gcc, no CUDA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
+                           _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.oracle_max_dist.restype = ctypes.c_int64
+        lib.oracle_max_dist.argtypes = [ctypes.c_int, i32p]
+        lib.oracle_edt2d.restype = ctypes.c_int
+        lib.oracle_edt2d.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p]
+        lib.oracle_edt3d.restype = ctypes.c_int
+        lib.oracle_edt3d.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, i32p, i32p]
+        lib.oracle_edt2d_basic.restype = ctypes.c_int
+        lib.oracle_edt2d_basic.argtypes = lib.oracle_edt2d.argtypes
+        lib.oracle_column_pass2d.restype = ctypes.c_int
+        lib.oracle_column_pass2d.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, i64p, i32p]
+        lib.oracle_envelope_state.restype = ctypes.c_long
+        lib.oracle_envelope_state.argtypes = [i64p, ctypes.c_long, ctypes.c_int64, i64p, i64p]
+        lib.oracle_sqrt_f32.restype = None
+        lib.oracle_sqrt_f32.argtypes = [i32p, ctypes.c_long, ctypes.POINTER(ctypes.c_float)]
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _mask(mask) -> np.ndarray:
+    m = np.ascontiguousarray(mask)
+    if m.dtype == np.bool_:
+        m = m.astype(np.uint8)
+    if m.dtype != np.uint8:
+        raise TypeError(f"mask must be uint8 or bool, got {m.dtype}")
+    return m
+
+
+def max_dist(shape) -> int:
+    """One more than the largest squared distance inside an image of `shape`."""
+    lib = _load()
+    s = np.ascontiguousarray(shape, dtype=np.int32)
+    return int(lib.oracle_max_dist(len(shape), _ptr(s, ctypes.c_int32)))
+
+
+def edt(mask, mode: int = TO_OBJECT, features: bool = True):
+    """Exact squared EDT of a 2-D or 3-D uint8 mask: returns (D, F) int32."""
+    lib = _load()
+    m = _mask(mask)
+    D = np.empty(m.shape, dtype=np.int32)
+    F = np.empty(m.shape, dtype=np.int32)
+    if m.ndim == 2:
+        rc = lib.oracle_edt2d(_ptr(m, ctypes.c_uint8), m.shape[0], m.shape[1], int(mode),
+                              _ptr(D, ctypes.c_int32), _ptr(F, ctypes.c_int32))
+    elif m.ndim == 3:
+        rc = lib.oracle_edt3d(_ptr(m, ctypes.c_uint8), m.shape[0], m.shape[1], m.shape[2],
+                              int(mode), _ptr(D, ctypes.c_int32), _ptr(F, ctypes.c_int32))
+    else:
+        raise ValueError("oracle handles 2-D and 3-D masks")
+    if rc != 0:
+        raise MemoryError("oracle ran out of memory")
+    return (D, F) if features else D
+
+
+def edt2d_basic(mask, mode: int = TO_OBJECT):
+    """Same result by the O(M L^2) row pass of Sec. 3.1 (cross-check)."""
+    lib = _load()
+    m = _mask(mask)
+    assert m.ndim == 2
+    D = np.empty(m.shape, dtype=np.int32)
+    F = np.empty(m.shape, dtype=np.int32)
+    rc = lib.oracle_edt2d_basic(_ptr(m, ctypes.c_uint8), m.shape[0], m.shape[1], int(mode),
+                                _ptr(D, ctypes.c_int32), _ptr(F, ctypes.c_int32))
+    if rc != 0:
+        raise MemoryError("oracle ran out of memory")
+    return D, F
+
+
+def column_pass(mask, mode: int = TO_OBJECT, down_only: bool = False):
+    """Column scans only: (Dv int64 with max_dist as infinity, G int32, max_dist)."""
+    lib = _load()
+    m = _mask(mask)
+    assert m.ndim == 2
+    Dv = np.empty(m.shape, dtype=np.int64)
+    G = np.empty(m.shape, dtype=np.int32)
+    lib.oracle_column_pass2d(_ptr(m, ctypes.c_uint8), m.shape[0], m.shape[1], int(mode),
+                             1 if down_only else 0, _ptr(Dv, ctypes.c_int64),
+                             _ptr(G, ctypes.c_int32))
+    return Dv, G, max_dist(m.shape)
+
+
+def envelope_state(f, maxd: int):
+    """First scan of Sec. 3.3.1 on one line: (ks, js) as 0-based int64 arrays."""
+    lib = _load()
+    fv = np.ascontiguousarray(f, dtype=np.int64)
+    n = fv.shape[0]
+    ks = np.empty(n + 1, dtype=np.int64)
+    js = np.empty(n + 2, dtype=np.int64)
+    cnt = lib.oracle_envelope_state(_ptr(fv, ctypes.c_int64), n, int(maxd),
+                                    _ptr(ks, ctypes.c_int64), _ptr(js, ctypes.c_int64))
+    return ks[:cnt].copy(), js[:cnt + 1].copy()
+
+
+def sqrt_f32(D) -> np.ndarray:
+    """float32 square root of the squared distances (+inf where D = INT32_MAX)."""
+    lib = _load()
+    d = np.ascontiguousarray(D, dtype=np.int32)
+    out = np.empty(d.shape, dtype=np.float32)
+    lib.oracle_sqrt_f32(_ptr(d, ctypes.c_int32), d.size, _ptr(out, ctypes.c_float))
+    return out

@@ -1,0 +1,38 @@
+"""Readers for the text fixtures under tests/golden (values transcribed from
+the paper; each file's header names the figure or passage it comes from)."""
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _lines(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                yield line
+
+
+def grid(name, inf=-1):
+    """Numeric grid; 'inf' cells become `inf` (an int sentinel)."""
+    rows = []
+    for line in _lines(name):
+        rows.append([inf if c == "inf" else int(c) for c in line.split()])
+    return np.array(rows, dtype=np.int64)
+
+
+def keyed(name):
+    """Lines of the form 'key v1 v2 ...' as a dict of string lists."""
+    out = {}
+    for line in _lines(name):
+        parts = line.split()
+        out[parts[0]] = parts[1:]
+    return out
+
+
+def six_object_mask():
+    """Fig. 18(a) as a uint8 mask (1 = object)."""
+    g = grid("fig18a_init.txt")
+    return (g == 0).astype(np.uint8)

@@ -1,0 +1,153 @@
+/*
+ * libedt -- exact squared Euclidean distance transform and feature map for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The operation (T. Strutz, "The Distance Transform and its Computation",
+ * Sec. 1.1 and Sec. 3): for a binary image or volume, every pixel p receives
+ *     D(p) = min over source pixels q of |p - q|^2          (Eq. (4))
+ * and F(p) = the 0-based row-major linear index of one source pixel q that
+ * attains D(p) (the Voronoi / feature map of Fig. 2 and Fig. 21's k*).
+ * Optionally dist(p) = the float32 nearest to sqrt(D(p)) (Sec. 3.1: the square
+ * root is drawn after all squared distances are known).
+ *
+ * Which pixels are sources is chosen by `mode` (Sec. 1.1, Fig. 1):
+ *     EDT_TO_OBJECT      sources are the nonzero mask bytes; background pixels
+ *                        get their distance to the nearest object (Fig. 1c),
+ *                        object pixels get 0;
+ *     EDT_TO_BACKGROUND  sources are the zero mask bytes; object pixels get
+ *                        their distance to the nearest background (Fig. 1b).
+ * Only pixels inside the image count (no virtual border).  An image without
+ * any source pixel yields D = INT32_MAX, F = -1 and dist = +inf everywhere.
+ * D is exact (bit-identical to the definition); where several sources are
+ * equally near, F names one of them.
+ *
+ * Conventions for every entry point:
+ *   - Masks are uint8, any nonzero byte is an object pixel, C order: a 2-D
+ *     mask is [H][W], a 3-D mask [Dz][H][W], unit isotropic spacing.
+ *   - Unless an entry point says otherwise, every pointer is DEVICE memory
+ *     owned by the caller; outputs must not overlap inputs or each other.
+ *   - Calls are asynchronous on the given CUDA stream (0 = legacy default
+ *     stream); results are ready when the stream reaches that point.
+ *   - Every call returns an edt_status; nothing throws or aborts across the
+ *     ABI.  edt_last_error() describes the last failure on the calling thread.
+ *   - Size limits (EDT_ERR_TOO_LARGE beyond them): every side <= 32767; a 2-D
+ *     row width W <= 16384 and a 3-D row width W <= 16384; fewer than 2^31
+ *     pixels in total; and the largest squared distance inside the image,
+ *     sum of (side - 1)^2, must stay below 2^31 - 1 so that D fits int32.
+ *   - Scratch memory: the plain calls draw their scratch from the device's
+ *     stream-ordered memory pool (cudaMallocAsync on the given stream, freed on
+ *     the same stream); batch plans and servers own theirs.
+ */
+#ifndef LIBEDT_EDT_H
+#define LIBEDT_EDT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *edt_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    EDT_OK = 0,
+    EDT_ERR_INVALID = 1,    /* null pointer, side <= 0, bad ndim or mode     */
+    EDT_ERR_TOO_LARGE = 2,  /* a size limit above is exceeded                 */
+    EDT_ERR_NOMEM = 3,      /* device or host allocation failed               */
+    EDT_ERR_CUDA = 4,       /* a CUDA runtime call or kernel launch failed    */
+    EDT_ERR_TIMEOUT = 5,    /* a bounded wait gave up                         */
+    EDT_ERR_BUDGET = 6,     /* a served job can never fit the memory budget   */
+    EDT_ERR_NOT_READY = 7   /* a served job has not finished yet              */
+} edt_status;
+
+enum { EDT_TO_OBJECT = 0, EDT_TO_BACKGROUND = 1 };
+
+/* Squared 2-D EDT (Sec. 3.1 column scans + Sec. 3.3.1 row envelope).
+ * mask: [H][W] uint8 (device); D: [H][W] int32 output (device). */
+edt_status edt_sq2d(const uint8_t *mask, int H, int W, int mode, int32_t *D,
+                    edt_stream_t stream);
+
+/* Squared 3-D EDT of a [Dz][H][W] volume (the same method applied along z,
+ * y and x; Sec. 3.1 "separate processing of all dimensions"). */
+edt_status edt_sq3d(const uint8_t *mask, int Dz, int H, int W, int mode,
+                    int32_t *D, edt_stream_t stream);
+
+/* Squared EDT plus feature map, 2-D (ndim = 2, shape = {H, W}) or 3-D
+ * (ndim = 3, shape = {Dz, H, W}).  F is required; D and dist may be NULL
+ * (dist = correctly rounded float32 sqrt(D), Sec. 3.1).  shape is a host
+ * pointer. */
+edt_status edt_feature(const uint8_t *mask, int ndim, const int *shape,
+                       int mode, int32_t *D, int32_t *F, float *dist,
+                       edt_stream_t stream);
+
+/* The same as edt_feature with HOST buffers: mask, D, F, dist are host
+ * pointers (pinned memory gives the fastest copies; pageable works).  The
+ * call copies the mask to the device, runs the transform, copies the
+ * results back and returns when they are in the host buffers.  Device
+ * buffers come from the stream-ordered pool of the current device. */
+edt_status edt_feature_host(const uint8_t *mask, int ndim, const int *shape,
+                            int mode, int32_t *D, int32_t *F, float *dist,
+                            edt_stream_t stream);
+
+/* One transform in a batch.  Pointers are device memory; F required, D and
+ * dist may be NULL; shape[2] is ignored for ndim = 2. */
+typedef struct {
+    const uint8_t *mask;
+    int ndim;
+    int shape[3];
+    int mode;
+    int32_t *D;
+    int32_t *F;
+    float *dist;
+} edt_job;
+
+typedef struct edt_plan edt_plan;
+
+/* A batch plan owns the device scratch and the CUDA graph that run up to
+ * n_max 2-D jobs in one replay.  `max_pixels` bounds the total pixel count
+ * of one batch (scratch is sized from it).  Not thread-safe: one plan per
+ * thread / stream. */
+edt_status edt_plan_create(edt_plan **plan, int n_max, int64_t max_pixels);
+edt_status edt_plan_destroy(edt_plan *plan);
+
+/* Run n jobs (n <= n_max) as one graph replay on `stream`: the job table is
+ * copied to the device and two batched kernels cover every job.  Results are
+ * bit-identical to n separate edt_feature calls.  2-D jobs only. */
+edt_status edt_batch(edt_plan *plan, const edt_job *jobs, int n,
+                     edt_stream_t stream);
+
+/* Continuous-batching server.  Jobs carry HOST pointers (mask in, D/F/dist
+ * out).  A scheduler thread admits jobs while their device footprint fits
+ * mem_budget_bytes, copies them in, groups the admitted jobs into batches,
+ * runs them on n_streams streams so that batches overlap, copies results out
+ * and completes the ticket.  Each result is identical to a plain edt_feature
+ * call on the same mask. */
+typedef struct edt_server edt_server;
+
+edt_status edt_serve_create(edt_server **server, size_t mem_budget_bytes,
+                            int n_streams);
+/* Queue one job; its host buffers must stay valid until the ticket is
+ * polled as done.  EDT_ERR_BUDGET when the job alone exceeds the budget. */
+edt_status edt_serve_submit(edt_server *server, const edt_job *job,
+                            uint64_t *ticket);
+/* EDT_OK when done (latency_s = seconds from submit to completion, may be
+ * NULL), EDT_ERR_NOT_READY while queued or running, another status when the
+ * job failed.  A finished ticket is forgotten after it was reported once. */
+edt_status edt_serve_poll(edt_server *server, uint64_t ticket,
+                          double *latency_s);
+/* Wait until every submitted job has finished, then stop the scheduler and
+ * free everything. */
+edt_status edt_serve_destroy(edt_server *server);
+
+/* Message of the last failure on the calling thread ("" when none). */
+const char *edt_last_error(void);
+
+/* Library version string. */
+const char *edt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBEDT_EDT_H */

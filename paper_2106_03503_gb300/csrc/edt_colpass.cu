@@ -1,0 +1,203 @@
+// Column pass of the exact EDT (Sec. 3.1 of Strutz, "The Distance Transform
+// and its Computation"): for every column, where are the source pixels, and
+// which source is nearest above and below each band of 32 rows.
+//
+// The paper's column pass propagates squared distances down and up each
+// column (Listing 7, Fig. 19, Fig. 18(b)).  Its result at row i of column j is
+// (i - g)^2 with g the nearest source row; here the same nearest row is
+// produced in a compact form that the row kernel expands on the fly:
+//   - one 32-bit word per (band of 32 rows, column) with the source bits,
+//     built by a warp from a 32 x 32 byte tile with 32 ballots (each lane
+//     loads 32 consecutive bytes of its own row; ballot t transposes byte t of
+//     all 32 rows into the word of column t);
+//   - per band, the nearest source row above and below it inside its group of
+//     32 bands, from a forward and a backward scan over the group's words;
+//   - per group, the nearest source above and below it over the whole column,
+//     computed by whichever warp of a 32-column tile finishes last (an arrival
+//     counter per tile; no warp ever waits for another).
+// A mask byte is read exactly once, with 16-byte loads where the row layout
+// allows it.
+#include "edt_engine.cuh"
+#include "edt_internal.h"
+
+namespace edt {
+
+constexpr int K1_WARPS = 4;
+
+ColGeom col_geom(int rows, int64_t cols)
+{
+    ColGeom g;
+    g.rows = rows;
+    g.cols = cols;
+    g.nb = (rows + 31) / 32;
+    g.nG = (g.nb + 31) / 32;
+    g.ntiles = (cols + 31) / 32;
+    return g;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t col_scratch_bytes(const ColGeom& g)
+{
+    const size_t c = (size_t)g.cols * 4;
+    return 2 * align256((size_t)g.nb * c) + 2 * align256((size_t)g.nG * c) +
+           align256((size_t)g.ntiles * 4);
+}
+
+ColScratch col_scratch_carve(void* base, const ColGeom& g)
+{
+    const size_t c = (size_t)g.cols * 4;
+    char* p = static_cast<char*>(base);
+    ColScratch s;
+    s.C = reinterpret_cast<uint32_t*>(p);
+    p += align256((size_t)g.nb * c);
+    s.U = reinterpret_cast<uint32_t*>(p);
+    p += align256((size_t)g.nb * c);
+    s.GFL = reinterpret_cast<uint32_t*>(p);
+    p += align256((size_t)g.nG * c);
+    s.GAB = reinterpret_cast<uint32_t*>(p);
+    p += align256((size_t)g.nG * c);
+    s.cnt = reinterpret_cast<unsigned*>(p);
+    return s;
+}
+
+// Bit t of the result is set when byte t of v is nonzero (t < 4).  The
+// per-byte compare gives 0xFF bytes; their top bits (7, 15, 23, 31) are moved
+// to bits 28..31 by one multiply (no two partial products overlap).
+__device__ __forceinline__ uint32_t nz_bits4(uint32_t v)
+{
+    const uint32_t x = __vcmpne4(v, 0u) & 0x80808080u;
+    return (x * 0x00204081u) >> 28;
+}
+
+__device__ __forceinline__ uint32_t nz_bits16(uint4 a)
+{
+    return nz_bits4(a.x) | (nz_bits4(a.y) << 4) | (nz_bits4(a.z) << 8) |
+           (nz_bits4(a.w) << 12);
+}
+
+// Source bits of the 32 bytes at p (only the first ncols are valid).
+template <bool VEC>
+__device__ __forceinline__ uint32_t load_row_bits(const uint8_t* __restrict__ p, int ncols)
+{
+    if (VEC && ncols == 32) {
+        const uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
+        const uint4 b = __ldcs(reinterpret_cast<const uint4*>(p + 16));
+        return nz_bits16(a) | (nz_bits16(b) << 16);
+    }
+    if (VEC && ncols == 16) {
+        const uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
+        return nz_bits16(a);
+    }
+    uint32_t bits = 0;
+    for (int t = 0; t < ncols; ++t) bits |= (uint32_t)(__ldcs(p + t) != 0) << t;
+    return bits;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(K1_WARPS * 32)
+k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s)
+{
+    __shared__ uint32_t cw[K1_WARPS][32][32];   // [warp][band][column]
+    __shared__ uint32_t upS[K1_WARPS][32][32];  // forward-scan results
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp;
+    if (gw >= g.ntiles * (int64_t)g.nG) return;  // whole warp; no block sync below
+    const int64_t tile = gw % g.ntiles;
+    const int G = (int)(gw / g.ntiles);
+    const int64_t W = g.cols;
+    const int64_t col0 = tile * 32;
+    const int64_t col = col0 + lane;
+    const int b0 = G * 32;
+    const int nbg = min(32, g.nb - b0);
+    const int ncols = (W - col0) < 32 ? (int)(W - col0) : 32;
+    const uint32_t colvalid = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
+
+    // (1) source bits of 32 rows x 32 columns per band, transposed by ballots
+    for (int bl = 0; bl < nbg; bl += 4) {
+        uint32_t src[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int row = (b0 + bl + u) * 32 + lane;
+            src[u] = 0;
+            if (bl + u < nbg && row < g.rows) {
+                src[u] = load_row_bits<VEC>(mask + (int64_t)row * W + col0, ncols);
+                if (mode == EDT_TO_BACKGROUND) src[u] = ~src[u];
+                src[u] &= colvalid;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (bl + u >= nbg) break;
+            uint32_t mine = 0;
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const uint32_t b = __ballot_sync(FULL, (src[u] >> t) & 1u);
+                if (lane == t) mine = b;
+            }
+            cw[warp][bl + u][lane] = mine;
+            if (col < W) s.C[(int64_t)(b0 + bl + u) * W + col] = mine;
+        }
+    }
+    __syncwarp();
+
+    // (2) nearest source above / below each band inside the group
+    if (col < W) {
+        int last = NONE16, first = NONE16;
+        for (int bl = 0; bl < nbg; ++bl) {
+            const uint32_t w = cw[warp][bl][lane];
+            upS[warp][bl][lane] = (uint32_t)last;
+            if (w) {
+                last = (b0 + bl) * 32 + 31 - __clz(w);
+                if (first == NONE16) first = (b0 + bl) * 32 + __ffs(w) - 1;
+            }
+        }
+        int nxt = NONE16;
+        for (int bl = nbg - 1; bl >= 0; --bl) {
+            const uint32_t w = cw[warp][bl][lane];
+            s.U[(int64_t)(b0 + bl) * W + col] = upS[warp][bl][lane] | ((uint32_t)nxt << 16);
+            if (w) nxt = (b0 + bl) * 32 + __ffs(w) - 1;
+        }
+        s.GFL[(int64_t)G * W + col] = (uint32_t)first | ((uint32_t)last << 16);
+    }
+
+    // (3) the last group of this tile to finish links the groups
+    __threadfence();
+    __syncwarp();
+    unsigned old = 0;
+    if (lane == 0) old = atomicAdd(&s.cnt[tile], 1u);
+    old = __shfl_sync(FULL, old, 0);
+    if (old != (unsigned)(g.nG - 1)) return;
+    __threadfence();
+    if (col < W) {
+        int above = NONE16;
+        for (int G2 = 0; G2 < g.nG; ++G2) {
+            const uint32_t v = __ldcg(s.GFL + (int64_t)G2 * W + col);
+            cw[warp][G2][lane] = (uint32_t)above;
+            if ((v >> 16) != (uint32_t)NONE16) above = (int)(v >> 16);
+        }
+        int below = NONE16;
+        for (int G2 = g.nG - 1; G2 >= 0; --G2) {
+            const uint32_t v = __ldcg(s.GFL + (int64_t)G2 * W + col);
+            s.GAB[(int64_t)G2 * W + col] = cw[warp][G2][lane] | ((uint32_t)below << 16);
+            if ((v & 0xFFFFu) != (uint32_t)NONE16) below = (int)(v & 0xFFFFu);
+        }
+    }
+    if (lane == 0) s.cnt[tile] = 0u;  // ready for the next call
+}
+
+cudaError_t launch_colbits(const uint8_t* mask, const ColGeom& g, int mode,
+                           const ColScratch& s, cudaStream_t stream)
+{
+    const int64_t warps = g.ntiles * (int64_t)g.nG;
+    const int64_t blocks = (warps + K1_WARPS - 1) / K1_WARPS;
+    const bool vec = (g.cols % 16 == 0) && ((reinterpret_cast<uintptr_t>(mask) & 15) == 0);
+    if (vec)
+        k_colbits<true><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s);
+    else
+        k_colbits<false><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s);
+    return cudaGetLastError();
+}
+
+}  // namespace edt

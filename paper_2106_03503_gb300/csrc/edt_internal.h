@@ -1,0 +1,75 @@
+// Internal declarations shared by the libedt translation units (host side).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/edt.h"
+
+namespace edt {
+
+// Scratch of the column pass for an image of `rows` x `cols` (rows = the
+// scanned axis).  All arrays are uint32 in device memory, `cols` wide:
+//   C    [nb][cols]  column-bit words, bit r = row 32*band + r is a source
+//   U    [nb][cols]  nearest source row above | below << 16 of each band,
+//                    looking only inside the band's group of 32 bands
+//                    (0xFFFF = none in the group)
+//   GFL  [nG][cols]  first | last << 16 source row of each group
+//   GAB  [nG][cols]  nearest source row above | below << 16 of each group,
+//                    over the whole column (0xFFFF = none)
+//   cnt  [ntiles]    arrival counters of the groups of one 32-column tile
+struct ColScratch {
+    uint32_t* C;
+    uint32_t* U;
+    uint32_t* GFL;
+    uint32_t* GAB;
+    unsigned* cnt;
+};
+
+struct ColGeom {
+    int rows;
+    int64_t cols;
+    int nb;        // bands of 32 rows
+    int nG;        // groups of 32 bands
+    int64_t ntiles;  // tiles of 32 columns
+};
+
+ColGeom col_geom(int rows, int64_t cols);
+size_t col_scratch_bytes(const ColGeom& g);
+ColScratch col_scratch_carve(void* base, const ColGeom& g);
+
+// Launchers (asynchronous on `stream`; return cudaGetLastError()).
+cudaError_t launch_colbits(const uint8_t* mask, const ColGeom& g, int mode,
+                           const ColScratch& s, cudaStream_t stream);
+cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
+                          int32_t* D, int32_t* F, float* dist, int sm_count,
+                          cudaStream_t stream);
+cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
+                           const ColScratch& s, uint32_t* P, cudaStream_t stream);
+cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,
+                           int32_t* F, float* dist, cudaStream_t stream);
+
+// Batched 2-D transforms (all jobs of a plan in two launches).
+struct BatchJobDev {
+    const uint8_t* mask;
+    int32_t* D;
+    int32_t* F;
+    float* dist;
+    int H, W, mode, nb, nG;
+    int64_t ntiles;
+    int64_t scratch_off;   // byte offset of this job's ColScratch
+    int64_t k1_first;      // first K1 warp index of this job
+    int64_t k2_first;      // first K2 block index of this job
+    int k2_rows;           // rows per K2 block
+    int pad_;
+};
+
+cudaError_t launch_batch(const BatchJobDev* jobs_dev, int njobs,
+                         int64_t k1_warps, int64_t k2_blocks, int max_W,
+                         void* scratch_base, cudaStream_t stream);
+
+cudaError_t set_2d_attributes();
+cudaError_t set_3d_attributes();
+
+}  // namespace edt

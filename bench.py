@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark: exact squared EDT + feature map (libedt) on GB300.
+
+Workload (one step): the 8192 x 8192 mask made of 2000 filled discs (integer
+centres uniform over the image, radii uniform 5..60, seed 2), transformed
+twice -- distances outside the discs (to object) and inside them (to
+background) -- each producing int32 squared distances D and the int32 feature
+map F.  2 * 8192^2 pixels per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` is whole-job Gpixel/s over the timed
+steps (CUDA events on the launching stream, L2 flushed between steps by
+writing a 256 MiB buffer, inputs resident in HBM).  `e2e` is the same metric
+through edt_feature_host with pinned host buffers (copies in the timed
+region).  `roofline` is the row-pass kernel k_rows2d, timed live by libedt's
+event tracing, against the measured HBM copy bandwidth.  `cpu_baseline` is the
+CPU oracle timed on this host on one full step.  With --impl reference the
+CPU oracle itself is the measured arm.
+
+Multi-GPU: the transform of one image does not exchange data across GPUs in
+this library ("replicas only"): with N GPUs every rank runs the same step on
+its own GPU and `value` counts all ranks' pixels over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpixel/s exact sq-EDT+feature map (bit-exact) batched vs plain; p99 latency"
+UNIT = "Gpixel/s"
+WORKLOAD = ("2D 8192x8192 uint8 mask = union of 2000 filled discs (centres uniform, radii "
+            "uniform integer 5-60, seed 2); inside (to background) and outside (to object) "
+            "transforms, int32 squared distances + int32 feature map")
+H = W = 8192
+K2_BYTES_PER_PX = 8          # algorithmic bytes of k_rows2d: D + F int32 stores
+PATH_BYTES_PER_PX = 9        # whole transform: 1 B mask read + 8 B stores
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def profile_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    that summary was taken on the current kernel sources (hash match)."""
+    try:
+        from paper_2106_03503_gb300 import build_lib
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)
+        entry = rec.get(kernel)
+        if not entry:
+            return None
+        h = hashlib.sha256()
+        for p in sorted(build_lib._sources()) + sorted(
+                f for f in build_lib._deps() if f.endswith((".cuh", ".h")) and "csrc" in f):
+            with open(p, "rb") as fh:
+                h.update(fh.read())
+        if entry.get("sources_sha256") != h.hexdigest():
+            return None
+        return entry.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5:
+            time.sleep(0.05)
+        self.lines = []  # keep only samples taken from now on
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in list(self.lines):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(mask, repeats=1):
+    """Gpixel/s of the oracle (single thread) on both transforms of `mask`."""
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        oracle.edt(mask, 0)
+        oracle.edt(mask, 1)
+    dt = time.perf_counter() - t0
+    return 2 * mask.size * repeats / dt / 1e9, dt
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the measured arm (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_2106_03503_gb300 import inputs
+    import oracle
+    oracle.build()
+    full = inputs.discs_8192()
+    rows = 1024
+    sample = full[:rows].copy()   # a full-width band: the same discs, density and widths
+    for _ in range(args.warmup):
+        oracle.edt(sample, 0)
+        oracle.edt(sample, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.edt(sample, 0)
+        oracle.edt(sample, 1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    px = 2 * sample.size
+    value = px * len(times) / total / 1e9
+    desc = (f"rows 0..{rows - 1} of the 8192x8192 discs mask ({rows}x8192), both transforms "
+            "per step, single-threaded C oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": desc, "parallelism": "cpu, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2106_03503_gb300 import build_lib, inputs
+    build_lib.build()
+    from paper_2106_03503_gb300 import edt
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    mask_np = inputs.discs_8192()
+    mask = torch.from_numpy(mask_np).to(dev)
+    D0 = torch.empty((H, W), dtype=torch.int32, device=dev)
+    F0 = torch.empty_like(D0)
+    D1 = torch.empty_like(D0)
+    F1 = torch.empty_like(D0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        edt.feature(mask, 0, out=(D0, F0, None))
+        edt.feature(mask, 1, out=(D1, F1, None))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if args.profile:
+        # the same kernels, nothing else: for ncu captures of this workload
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": "ok", "steps": args.steps}), flush=True)
+        return
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    edt.trace_enable(True)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                 # evict the mask and outputs from L2 (untimed)
+        starts[k].record(stream)
+        step()
+        stops[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    k2_ms, k2_n = edt.trace_read("k_rows2d")
+    k1_ms, k1_n = edt.trace_read("k_colbits")
+    edt.trace_enable(False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    px_step = 2 * H * W
+    value = px_step * args.steps * world / (total_ms / 1e3) / 1e9
+
+    # end to end through the public host-buffer entry point (pinned memory)
+    hmask = torch.from_numpy(mask_np).pin_memory()
+    hD = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
+    hF = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
+    e2e_steps = max(3, min(args.steps, 20))
+    for mode in (0, 1):
+        edt.feature_host(hmask, mode, D=hD[mode], F=hF[mode])
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for mode in (0, 1):
+            edt.feature_host(hmask, mode, D=hD[mode], F=hF[mode])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        barrier()
+    e2e_value = px_step * e2e_steps * world / e2e_s / 1e9
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        k2_avg_s = (k2_ms / max(k2_n, 1)) / 1e3
+        achieved = K2_BYTES_PER_PX * H * W / k2_avg_s / 1e9
+        traffic = profile_traffic("k_rows2d")
+        cpu_val, cpu_s = cpu_oracle_rate(mask_np)
+        sorted_ms = sorted(step_ms)
+        p50 = sorted_ms[len(sorted_ms) // 2]
+        p99 = sorted_ms[min(len(sorted_ms) - 1, int(round(0.99 * (len(sorted_ms) - 1))))]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pixels_per_step": px_step,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": p50, "p99": p99, "max": sorted_ms[-1]},
+            "effective_gbs_9B_per_px": value * PATH_BYTES_PER_PX,
+            "roofline": {"bound": "hbm", "kernel": "k_rows2d", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                         "bytes_per_px": K2_BYTES_PER_PX, "peak_source": peak_kind,
+                         "avg_launch_ms": k2_ms / max(k2_n, 1), "launches": k2_n,
+                         "k_colbits_avg_ms": k1_ms / max(k1_n, 1)},
+            "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one full step (both transforms of the 8192x8192 discs "
+                                       f"mask), single-threaded C oracle, {cpu_s:.1f} s"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * H * W,
+                    "d2h_bytes_per_step": 2 * 2 * 4 * H * W, "steps": e2e_steps,
+                    "api": "edt_feature_host, pinned host buffers"},
+            "gpu_launches": k1_n + k2_n,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="libedt", choices=["libedt", "reference"])
+    ap.add_argument("--profile", action="store_true",
+                    help="warm-up plus --steps steps of the workload only (for ncu)")
+    args = ap.parse_args()
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

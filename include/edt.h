@@ -31,7 +31,8 @@
  *   - Every call returns an edt_status; nothing throws or aborts across the
  *     ABI.  edt_last_error() describes the last failure on the calling thread.
  *   - Size limits (EDT_ERR_TOO_LARGE beyond them): every side <= 32767; a 2-D
- *     row width W <= 16384 and a 3-D row width W <= 16384; fewer than 2^31
+ *     row width W <= 16384; a 3-D volume H <= 2048 and W <= 1024 (a block
+ *     holds 32 whole lines of y resp. x in shared memory); fewer than 2^31
  *     pixels in total; and the largest squared distance inside the image,
  *     sum of (side - 1)^2, must stay below 2^31 - 1 so that D fits int32.
  *   - Scratch memory: the plain calls draw their scratch from the device's
@@ -139,6 +140,16 @@ edt_status edt_serve_poll(edt_server *server, uint64_t ticket,
 /* Wait until every submitted job has finished, then stop the scheduler and
  * free everything. */
 edt_status edt_serve_destroy(edt_server *server);
+
+/* Kernel timing for diagnostics and benchmarks.  While enabled, every kernel
+ * this library launches is bracketed by two CUDA events recorded on the
+ * stream it is launched on.  edt_trace_read waits for the recorded events and
+ * returns, for the kernel named `kernel` (e.g. "k_rows2d"), the summed elapsed
+ * milliseconds and the number of launches since tracing was last enabled.
+ * Enabling resets the record.  Costs two event records per launch. */
+edt_status edt_trace_enable(int on);
+edt_status edt_trace_read(const char *kernel, double *total_ms,
+                          int64_t *launches);
 
 /* Message of the last failure on the calling thread ("" when none). */
 const char *edt_last_error(void);

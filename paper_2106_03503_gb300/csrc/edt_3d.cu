@@ -10,7 +10,10 @@
 //   (x) the lower envelope along x over f(x') = (z - z')^2 + (y - y')^2 read
 //       from that record, writing D, F = z'*H*W + y'*W + x' and sqrt(D).
 // The (z', y') record lives in the caller's F (or D) buffer: the x pass reads
-// a row into shared memory before it overwrites the same row.
+// its rows into shared memory before it overwrites the same rows.
+// Both envelope passes use the band engine (edt_engine.cuh) with 32 lines per
+// block: 32 neighbouring x columns for the y pass (stores are coalesced across
+// lanes), 32 consecutive rows for the x pass (stores go through the tile).
 #include "edt_engine.cuh"
 #include "edt_internal.h"
 
@@ -21,63 +24,61 @@ constexpr uint32_t PNONE = 0xFFFFFFFFu;
 // --- y pass ----------------------------------------------------------------
 
 struct LineY {
-    int n;                   // H
-    const int* gz;           // padded [H]: nearest source z of (y', x), -1 none
-    int lg;
+    const short* gz;         // [H][32]: nearest source z of (y', x0 + lane), -1 none
+    int lane;
     int z;
     __device__ __forceinline__ bool eval(int k, int& f) const
     {
-        const int g = gz[pad_index(k, lg)];
+        const int g = gz[k * 32 + lane];
         if (g < 0) return false;
         f = (z - g) * (z - g);
         return true;
     }
     __device__ __forceinline__ int c(int k) const
     {
-        const int g = gz[pad_index(k, lg)];
+        const int g = gz[k * 32 + lane];
         return (z - g) * (z - g) + k * k;
     }
     __device__ __forceinline__ int feature(int k) const
     {
-        return (int)(((uint32_t)gz[pad_index(k, lg)] << 16) | (uint32_t)k);
+        return (int)(((uint32_t)gz[k * 32 + lane] << 16) | (uint32_t)k);
     }
 };
 
 struct OutY {
-    uint32_t* tile;          // [H][XT + 1]
-    int TP;                  // tile pitch, XT + 1
-    int xl;
-    __device__ __forceinline__ void store(int j, int v, int f) const
+    uint32_t* P;             // record of voxel (z, y, x0 + lane) at P[y * W]
+    int W;
+    bool valid;
+    __device__ __forceinline__ void store(int ln, int j, int v, int f) const
     {
-        tile[j * TP + xl] = (v == INT32_MAX) ? PNONE : (uint32_t)f;
+        (void)ln;
+        if (valid) P[(int64_t)j * W] = (v == INT32_MAX) ? PNONE : (uint32_t)f;
     }
 };
 
-// One block: one z, XT consecutive x (one warp per x line).
+static size_t ypass_smem(int H, int lg, int NW)
+{
+    return (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5, false);
+}
+
+// One block: one z, 32 consecutive x (one line per lane), warps = y segments.
 __global__ void __launch_bounds__(1024)
-k_ypass3d(int Dz, int H, int W, ColScratch s, int XT, uint32_t* __restrict__ P)
+k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lg = seg_log2(H);
-    const int SW = ((1 << lg) + 31) / 32;
-    const int pitch = padded_len(H) | 1;       // odd: conflict-free fills
-    int* gz = reinterpret_cast<int*>(smem);    // [XT][pitch]
-    const int TP = XT + 1;
-    uint32_t* tile = reinterpret_cast<uint32_t*>(gz + XT * pitch);   // [H][TP]
-    unsigned char* wbase = reinterpret_cast<unsigned char*>(tile + (size_t)H * TP);
-    wbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(wbase) + 15) & ~uintptr_t(15));
-    const int warp = threadIdx.x >> 5;
+    short* gz = reinterpret_cast<short*>(smem);
+    const BandSmem sm = carve_band_smem(smem + (((size_t)H * 32 * 2 + 15) & ~size_t(15)), NW,
+                                        (1 << lg) >> 5, false);
     const int lane = threadIdx.x & 31;
-
-    const int xtiles = (W + XT - 1) / XT;
+    const int xtiles = (W + 31) / 32;
     const int z = blockIdx.x / xtiles;
-    const int x0 = (blockIdx.x % xtiles) * XT;
+    const int x0 = (blockIdx.x % xtiles) * 32;
     const int64_t plane = (int64_t)H * W;
     const int zb = z >> 5, zr = z & 31, zG = zb >> 5;
 
-    // nearest source along z for every (y, x) of the tile
-    for (int e = threadIdx.x; e < H * XT; e += blockDim.x) {
-        const int y = e / XT, xl = e % XT, x = x0 + xl;
+    // nearest source along z of every (y, x) of the tile
+    for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {
+        const int y = e >> 5, xl = e & 31, x = x0 + xl;
         int g = -1;
         if (x < W) {
             const int64_t p = (int64_t)y * W + x;
@@ -91,37 +92,25 @@ k_ypass3d(int Dz, int H, int W, ColScratch s, int XT, uint32_t* __restrict__ P)
             }
             g = nearest_in_column(w, zb * 32, zr, (int)up, (int)dn);
         }
-        gz[xl * pitch + pad_index(y, lg)] = g;
+        gz[e] = (short)g;
     }
     __syncthreads();
 
-    if (warp < XT && x0 + warp < W) {
-        const WarpSmem sm = carve_warp_smem(wbase + warp * warp_smem_bytes(SW), SW);
-        const LineY line{H, gz + warp * pitch, lg, z};
-        const OutY out{tile, TP, warp};
-        warp_envelope(line, out, sm);
-    }
-    __syncthreads();
-
-    // coalesced write of the (z', y') records
-    for (int e = threadIdx.x; e < H * XT; e += blockDim.x) {
-        const int y = e / XT, xl = e % XT, x = x0 + xl;
-        if (x < W) P[(int64_t)z * plane + (int64_t)y * W + x] = tile[y * TP + xl];
-    }
-    (void)lane;
-    (void)Dz;
+    const LineY line{gz, lane, z};
+    const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
+    band_envelope<false>(line, out, sm, H, lg, NW);
 }
 
 // --- x pass ----------------------------------------------------------------
 
 struct LineX {
-    int n;                   // W
-    const uint32_t* rec;     // padded [W]: (z', y') records of this row
-    int lg;
+    const uint32_t* rec;     // this lane's row of (z', y') records (pitch odd)
     int z, y, H, W;
+    bool valid;
     __device__ __forceinline__ bool eval(int k, int& f) const
     {
-        const uint32_t p = rec[pad_index(k, lg)];
+        if (!valid) return false;
+        const uint32_t p = rec[k];
         if (p == PNONE) return false;
         const int dz = z - (int)(p >> 16), dy = y - (int)(p & 0xFFFFu);
         f = dz * dz + dy * dy;
@@ -129,13 +118,13 @@ struct LineX {
     }
     __device__ __forceinline__ int c(int k) const
     {
-        int f;
-        eval(k, f);
-        return f + k * k;
+        const uint32_t p = rec[k];
+        const int dz = z - (int)(p >> 16), dy = y - (int)(p & 0xFFFFu);
+        return dz * dz + dy * dy + k * k;
     }
     __device__ __forceinline__ int feature(int k) const
     {
-        const uint32_t p = rec[pad_index(k, lg)];
+        const uint32_t p = rec[k];
         return ((int)(p >> 16) * H + (int)(p & 0xFFFFu)) * W + k;
     }
 };
@@ -144,45 +133,67 @@ struct OutX {
     int32_t* D;
     int32_t* F;
     float* dist;
-    int64_t rowoff;
-    __device__ __forceinline__ void store(int j, int v, int f) const
+    int64_t row0, nrows;
+    int W;
+    __device__ __forceinline__ void store(int ln, int j, int v, int f) const
     {
-        const int64_t i = rowoff + j;
+        const int64_t row = row0 + ln;
+        if (row >= nrows) return;
+        const int64_t i = row * W + j;
         if (D) D[i] = v;
         if (F) F[i] = f;
         if (dist) dist[i] = sqrt_rn_int(v);
     }
 };
 
-// One block: `rows` consecutive rows (z, y) ... of the volume, one warp each.
-__global__ void __launch_bounds__(256)
-k_xpass3d(int Dz, int H, int W, int rows, const uint32_t* P, int32_t* D,
+static int xpass_pitch(int W) { return W | 1; }
+
+static size_t xpass_smem(int W, int lg, int NW)
+{
+    return (((size_t)32 * xpass_pitch(W) * 4 + 15) & ~size_t(15)) +
+           band_smem_bytes(NW, (1 << lg) >> 5, true);
+}
+
+// One block: 32 consecutive rows (z, y) of the volume (one per lane), warps =
+// x segments.
+__global__ void __launch_bounds__(1024)
+k_xpass3d(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D,
           int32_t* F, float* dist)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lg = seg_log2(W);
-    const int SW = ((1 << lg) + 31) / 32;
-    const int np = padded_len(W);
-    uint32_t* rec = reinterpret_cast<uint32_t*>(smem);   // [rows][np]
-    unsigned char* wbase = smem + (((size_t)rows * np * 4 + 15) & ~size_t(15));
-    const int warp = threadIdx.x >> 5;
+    const int pitch = W | 1;
+    uint32_t* rec = reinterpret_cast<uint32_t*>(smem);   // [32][pitch]
+    const BandSmem sm = carve_band_smem(smem + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)), NW,
+                                        (1 << lg) >> 5, true);
+    const int lane = threadIdx.x & 31;
     const int64_t nrows = (int64_t)Dz * H;
-    const int64_t row0 = (int64_t)blockIdx.x * rows;
+    const int64_t row0 = (int64_t)blockIdx.x * 32;
 
-    for (int e = threadIdx.x; e < rows * W; e += blockDim.x) {
-        const int rl = e / W, k = e % W;
+    for (int e = threadIdx.x; e < 32 * W; e += blockDim.x) {
+        const int rl = e / W, k = e - rl * W;
         const int64_t row = row0 + rl;
-        if (row < nrows) rec[rl * np + pad_index(k, lg)] = P[row * W + k];
+        rec[rl * pitch + k] = (row < nrows) ? P[row * W + k] : PNONE;
     }
     __syncthreads();
 
-    const int64_t row = row0 + warp;
-    if (warp < rows && row < nrows) {
-        const WarpSmem sm = carve_warp_smem(wbase + warp * warp_smem_bytes(SW), SW);
-        const int z = (int)(row / H), y = (int)(row % H);
-        const LineX line{W, rec + warp * np, lg, z, y, H, W};
-        const OutX out{D, F, dist, row * W};
-        warp_envelope(line, out, sm);
+    const int64_t row = row0 + lane;
+    LineX line;
+    line.rec = rec + lane * pitch;
+    line.z = (int)(row / H);
+    line.y = (int)(row % H);
+    line.H = H;
+    line.W = W;
+    line.valid = row < nrows;
+    const OutX out{D, F, dist, row0, nrows, W};
+    band_envelope<true>(line, out, sm, W, lg, NW);
+}
+
+static void pick_band(int n, size_t (*smem_fn)(int, int, int), int& lg, int& NW)
+{
+    for (int max_nw = 32; max_nw >= 1; max_nw >>= 1) {
+        lg = band_seg_log2(n, max_nw);
+        NW = (n + (1 << lg) - 1) >> lg;
+        if (smem_fn(n, lg, NW) <= 227 * 1024) return;
     }
 }
 
@@ -190,33 +201,22 @@ cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
                            const ColScratch& s, uint32_t* P, cudaStream_t stream)
 {
     (void)g;
-    const int lg = seg_log2(H);
-    const int SW = ((1 << lg) + 31) / 32;
-    const int pitch = padded_len(H) | 1;
-    int XT = 32;
-    auto smem_for = [&](int xt) {
-        return (size_t)xt * pitch * 4 + (size_t)H * (xt + 1) * 4 + 16 + (size_t)xt * warp_smem_bytes(SW);
-    };
-    while (XT > 1 && smem_for(XT) > 200 * 1024) XT >>= 1;
-    const size_t smem = smem_for(XT);
-    const int xtiles = (W + XT - 1) / XT;
+    int lg, NW;
+    pick_band(H, ypass_smem, lg, NW);
+    const int xtiles = (W + 31) / 32;
     const unsigned blocks = (unsigned)((int64_t)Dz * xtiles);
-    k_ypass3d<<<blocks, XT * 32, smem, stream>>>(Dz, H, W, s, XT, P);
+    k_ypass3d<<<blocks, NW * 32, ypass_smem(H, lg, NW), stream>>>(H, W, s, lg, NW, P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,
                            int32_t* F, float* dist, cudaStream_t stream)
 {
-    const int lg = seg_log2(W);
-    const int SW = ((1 << lg) + 31) / 32;
-    const int np = padded_len(W);
-    int rows = 8;
-    while (rows > 1 && (size_t)rows * (np * 4 + warp_smem_bytes(SW)) > 200 * 1024) rows >>= 1;
-    const size_t smem = (((size_t)rows * np * 4 + 15) & ~size_t(15)) + (size_t)rows * warp_smem_bytes(SW);
+    int lg, NW;
+    pick_band(W, xpass_smem, lg, NW);
     const int64_t nrows = (int64_t)Dz * H;
-    const unsigned blocks = (unsigned)((nrows + rows - 1) / rows);
-    k_xpass3d<<<blocks, rows * 32, smem, stream>>>(Dz, H, W, rows, P, D, F, dist);
+    const unsigned blocks = (unsigned)((nrows + 31) / 32);
+    k_xpass3d<<<blocks, NW * 32, xpass_smem(W, lg, NW), stream>>>(Dz, H, W, lg, NW, P, D, F, dist);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "edt_internal.h"
 
@@ -83,7 +84,8 @@ edt_status check_shape(int ndim, const int* shape, int mode)
         return fail(EDT_ERR_TOO_LARGE, "largest squared distance %lld does not fit int32", (long long)maxsq);
     const int W = shape[ndim - 1];
     if (W > 16384) return fail(EDT_ERR_TOO_LARGE, "row width %d exceeds 16384", W);
-    if (ndim == 3 && shape[1] > 8192) return fail(EDT_ERR_TOO_LARGE, "3-D height %d exceeds 8192", shape[1]);
+    if (ndim == 3 && shape[1] > 2048) return fail(EDT_ERR_TOO_LARGE, "3-D height %d exceeds 2048", shape[1]);
+    if (ndim == 3 && W > 1024) return fail(EDT_ERR_TOO_LARGE, "3-D row width %d exceeds 1024", W);
     return EDT_OK;
 }
 
@@ -107,9 +109,10 @@ edt_status run_transform(const uint8_t* mask, int ndim, const int* shape, int mo
         const ColScratch s = col_scratch_carve(scratch, g);
         if ((e = cudaMemsetAsync(s.cnt, 0, (size_t)g.ntiles * 4, stream)) != cudaSuccess)
             return cuda_fail(e, "cudaMemsetAsync");
-        if ((e = launch_colbits(mask, g, mode, s, stream)) != cudaSuccess)
+        if ((e = traced("k_colbits", stream, [&] { return launch_colbits(mask, g, mode, s, stream); })) != cudaSuccess)
             return cuda_fail(e, "column pass launch");
-        if ((e = launch_rows2d(H, W, g, s, D, F, dist, sm_count, stream)) != cudaSuccess)
+        if ((e = traced("k_rows2d", stream,
+                        [&] { return launch_rows2d(H, W, g, s, D, F, dist, sm_count, stream); })) != cudaSuccess)
             return cuda_fail(e, "row pass launch");
         return EDT_OK;
     }
@@ -119,13 +122,64 @@ edt_status run_transform(const uint8_t* mask, int ndim, const int* shape, int mo
     uint32_t* P = reinterpret_cast<uint32_t*>(F ? F : D);
     if ((e = cudaMemsetAsync(s.cnt, 0, (size_t)g.ntiles * 4, stream)) != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync");
-    if ((e = launch_colbits(mask, g, mode, s, stream)) != cudaSuccess)
+    if ((e = traced("k_colbits", stream, [&] { return launch_colbits(mask, g, mode, s, stream); })) != cudaSuccess)
         return cuda_fail(e, "z pass launch");
-    if ((e = launch_ypass3d(Dz, H, W, g, s, P, stream)) != cudaSuccess)
+    if ((e = traced("k_ypass3d", stream, [&] { return launch_ypass3d(Dz, H, W, g, s, P, stream); })) != cudaSuccess)
         return cuda_fail(e, "y pass launch");
-    if ((e = launch_xpass3d(Dz, H, W, P, D, F, dist, stream)) != cudaSuccess)
+    if ((e = traced("k_xpass3d", stream,
+                    [&] { return launch_xpass3d(Dz, H, W, P, D, F, dist, stream); })) != cudaSuccess)
         return cuda_fail(e, "x pass launch");
     return EDT_OK;
+}
+
+// --- kernel tracing ---------------------------------------------------------
+
+struct TraceRec {
+    const char* kernel;
+    cudaEvent_t start, stop;
+};
+static std::mutex g_trace_mu;
+static std::atomic<bool> g_trace_on{false};
+static std::vector<TraceRec> g_trace;        // recorded launches
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t pooled_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t ev = g_event_pool.back();
+        g_event_pool.pop_back();
+        return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    cudaEventCreate(&ev);
+    return ev;
+}
+
+bool trace_on() { return g_trace_on.load(std::memory_order_relaxed); }
+
+int trace_begin(const char* kernel, cudaStream_t stream)
+{
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    TraceRec r{kernel, pooled_event(), pooled_event()};
+    cudaEventRecord(r.start, stream);
+    g_trace.push_back(r);
+    return (int)g_trace.size() - 1;
+}
+
+void trace_end(int slot, cudaStream_t stream)
+{
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (slot >= 0 && slot < (int)g_trace.size()) cudaEventRecord(g_trace[slot].stop, stream);
+}
+
+static void trace_reset_locked()
+{
+    for (auto& r : g_trace) {
+        cudaEventSynchronize(r.stop);
+        g_event_pool.push_back(r.start);
+        g_event_pool.push_back(r.stop);
+    }
+    g_trace.clear();
 }
 
 // One transform with scratch from the stream-ordered pool.
@@ -221,6 +275,35 @@ edt_status edt_feature_host(const uint8_t* mask, int ndim, const int* shape,
     if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
     if (st == EDT_OK) clear_error();
     return st;
+}
+
+edt_status edt_trace_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    trace_reset_locked();
+    g_trace_on.store(on != 0);
+    return EDT_OK;
+}
+
+edt_status edt_trace_read(const char* kernel, double* total_ms, int64_t* launches)
+{
+    if (!kernel || !total_ms || !launches) return fail(EDT_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    double ms = 0.0;
+    int64_t n = 0;
+    for (auto& r : g_trace) {
+        if (strcmp(r.kernel, kernel) != 0) continue;
+        cudaError_t e = cudaEventSynchronize(r.stop);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, r.start, r.stop);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        ms += t;
+        ++n;
+    }
+    *total_ms = ms;
+    *launches = n;
+    return EDT_OK;
 }
 
 const char* edt_last_error(void) { return g_err.c_str(); }

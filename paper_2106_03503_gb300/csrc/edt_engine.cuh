@@ -1,6 +1,6 @@
-// Device building blocks of libedt (sm_103a): the warp-level lower envelope
-// of parabolas along one line (Sec. 3.3.1 of Strutz, "The Distance Transform
-// and its Computation"), the bit tricks of the column pass (Sec. 3.1) and the
+// Device building blocks of libedt (sm_103a): the lower envelope of parabolas
+// along many lines at once (Sec. 3.3.1 of Strutz, "The Distance Transform and
+// its Computation"), the bit tricks of the column pass (Sec. 3.1) and the
 // correctly rounded float32 square root.
 //
 // Lower envelope as a lower convex hull.  For one line, parabola k is
@@ -15,20 +15,29 @@
 // paper's listing compares ceilings of the intersections instead; both give
 // the same lower envelope at integer positions, ties aside.)
 //
-// Work split.  One warp handles one line of n values.  Lane l owns the
-// contiguous segment [l*S, l*S + S).  (1) Each lane builds the hull of its
-// segment with the paper's stack algorithm, the stack kept as a bit set in
-// shared memory (bit = column is on the hull).  (2) Five rounds of pairwise
-// merges join neighbouring lanes' hulls: for two x-separated lower hulls the
-// joint hull keeps a prefix of the left one and a suffix of the right one,
-// found by the classic bridge walk (drop the left top while it is hidden
-// between its predecessor and the right bottom, drop the right bottom while it
-// is hidden between the left top and its successor).  (3) Each lane fills its
-// own columns: the owner of a column is the hull member with the smallest
-// value there; owners move right monotonically with the column, and along
-// the hull the values at a fixed column are unimodal, so a walk finds them.
-// Results go through a small per-warp shared tile so that global stores are
-// written in whole 32-byte sectors.
+// Work split ("band engine").  A block processes 32 lines together, lane l
+// of every warp working on line l, and the NW warps split the positions of
+// the lines into NW segments of SEG = 2^lg positions.  So all lanes of a warp
+// step through the same position k at the same time: data shared by the 32
+// lines at position k (the column words of a band of 32 rows, say) is one
+// broadcast shared-memory read, and only the per-line arithmetic differs.
+//   (1) Each (segment, line) builds the hull of its own positions with the
+//       paper's stack algorithm (pop while the top is hidden, then push); the
+//       stack is a bit set in shared memory (bit = position is on the hull)
+//       plus the top two entries in registers.
+//   (2) log2(NW) rounds of pairwise merges join neighbouring segments' hulls,
+//       every lane on its own line: for two x-separated lower hulls the joint
+//       hull keeps a prefix of the left and a suffix of the right one, found
+//       by the classic bridge walk (drop the left top while it is hidden
+//       between its predecessor and the right bottom; drop the right bottom
+//       while it is hidden between the left top and its successor).
+//   (3) Each (segment, line) fills its positions: the owner of a position is
+//       the hull member with the smallest value there; owners move right
+//       monotonically with the position, and along the hull the values at a
+//       fixed position are unimodal, so a walk finds them.  Values either go
+//       straight to memory (lines adjacent in memory) or through a 32 x 8
+//       shared tile that turns them into 32-byte row segments (lines are
+//       rows, positions are columns).
 #pragma once
 
 #include <cstdint>
@@ -99,49 +108,43 @@ __device__ __forceinline__ int nearest_in_column(uint32_t w, int base, int r,
 }
 
 // ---------------------------------------------------------------------------
-// Lower-envelope engine.
+// Band engine.
 
-struct WarpSmem {
-    uint32_t* hb;   // hull bits, layout [word][lane], SW words per lane
-    int* lo;        // first hull member of each lane (-1 = none)
-    int* hi;        // last hull member of each lane
-    int* tileD;     // 32 x OUT_CHUNK staging tile for values
-    int* tileF;     // 32 x OUT_CHUNK staging tile for features
+constexpr int OC = 8;   // positions per fill round (tile width)
+
+struct BandSmem {
+    uint32_t* hb;   // [NW][SEGW][32] hull bits: segment, word, lane
+    int* lo;        // [NW][32] first hull member of (segment, line), -1 none
+    int* hi;        // [NW][32] last hull member
+    int* tileD;     // [NW][32][OC] staging of values (tiled output only)
+    int* tileF;     // [NW][32][OC] staging of features
 };
 
-// Bytes of shared memory one warp needs for a line with SW hull words/lane.
-__host__ __device__ constexpr int warp_smem_bytes(int SW)
+__host__ __device__ inline size_t band_smem_bytes(int NW, int SEGW, bool tiled)
 {
-    return SW * 32 * 4 + 64 * 4 + 2 * 32 * OUT_CHUNK * 4;
+    return (size_t)NW * SEGW * 32 * 4 + (size_t)NW * 64 * 4 +
+           (tiled ? (size_t)NW * 32 * OC * 4 * 2 : 0);
 }
 
-__device__ __forceinline__ WarpSmem carve_warp_smem(unsigned char* base, int SW)
+__device__ __forceinline__ BandSmem carve_band_smem(unsigned char* base, int NW, int SEGW, bool tiled)
 {
-    WarpSmem s;
+    BandSmem s;
     s.hb = reinterpret_cast<uint32_t*>(base);
-    s.lo = reinterpret_cast<int*>(base + SW * 32 * 4);
-    s.hi = s.lo + 32;
-    s.tileD = s.hi + 32;
-    s.tileF = s.tileD + 32 * OUT_CHUNK;
+    s.lo = reinterpret_cast<int*>(base + (size_t)NW * SEGW * 32 * 4);
+    s.hi = s.lo + NW * 32;
+    s.tileD = tiled ? s.hi + NW * 32 : nullptr;
+    s.tileF = tiled ? s.tileD + NW * 32 * OC : nullptr;
     return s;
 }
 
-// Segment length per lane: the smallest power of two >= max(OUT_CHUNK,
-// ceil(n / 32)), so that lane = column >> log2(S).  Hull words per lane: S/32.
-__host__ __device__ inline int seg_log2(int n)
+// Segment length (power of two, >= 32) and segment count for a line of n
+// positions split over at most max_nw warps.
+__host__ __device__ inline int band_seg_log2(int n, int max_nw)
 {
-    int s = (n + 31) / 32;
-    int l = 3;  // OUT_CHUNK = 8
-    while ((1 << l) < s) ++l;
-    return l;
+    int lg = 5;
+    while ((((n + (1 << lg) - 1) >> lg)) > max_nw) ++lg;
+    return lg;
 }
-__host__ __device__ inline int seg_len(int n) { return 1 << seg_log2(n); }
-__host__ __device__ inline int seg_words(int n) { return (seg_len(n) + 31) / 32; }
-// Shared-memory index of column k when lane segments of length S = 2^lg are
-// stored back to back: one pad word per segment puts the 32 lanes' columns at
-// the same offset into 32 different banks (S + 1 is odd).
-__host__ __device__ __forceinline__ int pad_index(int k, int lg) { return k + (k >> lg); }
-__host__ __device__ inline int padded_len(int n) { return n + (n >> seg_log2(n)) + 1; }
 
 // t is hidden between p < t < m on the hull of points (k, c_k).
 __device__ __forceinline__ bool hidden(int p, int cp, int t, int ct, int m, int cm)
@@ -150,83 +153,86 @@ __device__ __forceinline__ bool hidden(int p, int cp, int t, int ct, int m, int 
            (long long)(ct - cp) * (long long)(m - t);
 }
 
-// Previous / next hull member of lane L strictly before / after column x
-// (x must lie in L's segment).  -1 when none.
-__device__ __forceinline__ int prev_in_lane(const uint32_t* hb, int L, int S, int x)
+// Previous / next hull member of (segment s, this lane) strictly before /
+// after position x of that segment; -1 when none.
+__device__ __forceinline__ int seg_prev(const uint32_t* hb, int s, int lg, int SEGW, int lane, int x)
 {
-    const int off = x - L * S;
+    const int off = x - (s << lg);
     int w = off >> 5;
-    const int b = off & 31;
-    uint32_t m = hb[w * 32 + L] & ((1u << b) - 1u);
+    const uint32_t* base = hb + (size_t)s * SEGW * 32 + lane;
+    uint32_t m = base[w * 32] & ((1u << (off & 31)) - 1u);
     while (!m) {
         if (--w < 0) return -1;
-        m = hb[w * 32 + L];
+        m = base[w * 32];
     }
-    return L * S + w * 32 + 31 - __clz(m);
+    return (s << lg) + w * 32 + 31 - __clz(m);
 }
-__device__ __forceinline__ int next_in_lane(const uint32_t* hb, int L, int S, int SW, int x)
+__device__ __forceinline__ int seg_next(const uint32_t* hb, int s, int lg, int SEGW, int lane, int x)
 {
-    const int off = x - L * S;
+    const int off = x - (s << lg);
     int w = off >> 5;
     const int b = off & 31;
-    uint32_t m = (b == 31) ? 0u : (hb[w * 32 + L] & (0xFFFFFFFEu << b));
+    const uint32_t* base = hb + (size_t)s * SEGW * 32 + lane;
+    uint32_t m = (b == 31) ? 0u : (base[w * 32] & (0xFFFFFFFEu << b));
     while (!m) {
-        if (++w >= SW) return -1;
-        m = hb[w * 32 + L];
+        if (++w >= SEGW) return -1;
+        m = base[w * 32];
     }
-    return L * S + w * 32 + __ffs(m) - 1;
+    return (s << lg) + w * 32 + __ffs(m) - 1;
 }
 
-// Join the hulls of lanes [a0, b0) and [b0, b1) (run by one lane).
+// Join the hulls of segments [a0, b0) and [b0, b1) of this lane's line.
 template <class Line>
-__device__ void bridge(const Line& line, uint32_t* hb, int* lo, int* hi, int S,
-                       int SW, int a0, int b0, int b1)
+__device__ void band_bridge(const Line& line, const BandSmem& sm, int lg, int SEGW, int lane,
+                            int a0, int b0, int b1)
 {
+    int* lo = sm.lo + lane;
+    int* hi = sm.hi + lane;
     int la = b0 - 1;
-    while (la >= a0 && hi[la] < 0) --la;
+    while (la >= a0 && hi[la * 32] < 0) --la;
     int lb = b0;
-    while (lb < b1 && lo[lb] < 0) ++lb;
+    while (lb < b1 && lo[lb * 32] < 0) ++lb;
     while (la >= a0 && lb < b1) {
-        const int x1 = hi[la];
-        const int y1 = lo[lb];
-        int x0 = prev_in_lane(hb, la, S, x1);
+        const int x1 = hi[la * 32];
+        const int y1 = lo[lb * 32];
+        int x0 = seg_prev(sm.hb, la, lg, SEGW, lane, x1);
         int lx0 = la;
         if (x0 < 0) {
             int l = la - 1;
-            while (l >= a0 && hi[l] < 0) --l;
-            if (l >= a0) { x0 = hi[l]; lx0 = l; }
+            while (l >= a0 && hi[l * 32] < 0) --l;
+            if (l >= a0) { x0 = hi[l * 32]; lx0 = l; }
         }
-        int y2 = next_in_lane(hb, lb, S, SW, y1);
+        int y2 = seg_next(sm.hb, lb, lg, SEGW, lane, y1);
         const bool y2_same = (y2 >= 0);
         if (y2 < 0) {
             int l = lb + 1;
-            while (l < b1 && lo[l] < 0) ++l;
-            if (l < b1) y2 = lo[l];
+            while (l < b1 && lo[l * 32] < 0) ++l;
+            if (l < b1) y2 = lo[l * 32];
         }
         const int cx1 = line.c(x1);
         const int cy1 = line.c(y1);
         if (x0 >= 0 && hidden(x0, line.c(x0), x1, cx1, y1, cy1)) {
-            const int off = x1 - la * S;
-            hb[(off >> 5) * 32 + la] &= ~(1u << (off & 31));
+            const int off = x1 - (la << lg);
+            sm.hb[((size_t)la * SEGW + (off >> 5)) * 32 + lane] &= ~(1u << (off & 31));
             if (lx0 == la) {
-                hi[la] = x0;
+                hi[la * 32] = x0;
             } else {
-                hi[la] = -1;
-                lo[la] = -1;
+                hi[la * 32] = -1;
+                lo[la * 32] = -1;
                 la = lx0;
             }
             continue;
         }
         if (y2 >= 0 && hidden(x1, cx1, y1, cy1, y2, line.c(y2))) {
-            const int off = y1 - lb * S;
-            hb[(off >> 5) * 32 + lb] &= ~(1u << (off & 31));
+            const int off = y1 - (lb << lg);
+            sm.hb[((size_t)lb * SEGW + (off >> 5)) * 32 + lane] &= ~(1u << (off & 31));
             if (y2_same) {
-                lo[lb] = y2;
+                lo[lb * 32] = y2;
             } else {
-                lo[lb] = -1;
-                hi[lb] = -1;
+                lo[lb * 32] = -1;
+                hi[lb * 32] = -1;
                 ++lb;
-                while (lb < b1 && lo[lb] < 0) ++lb;
+                while (lb < b1 && lo[lb * 32] < 0) ++lb;
             }
             continue;
         }
@@ -234,48 +240,48 @@ __device__ void bridge(const Line& line, uint32_t* hb, int* lo, int* hi, int S,
     }
 }
 
-// Global successor / predecessor of hull member x after the merge.
-__device__ __forceinline__ int hull_next(const uint32_t* hb, const int* lo,
-                                         uint32_t nonempty, int S, int SW, int x)
+// Successor / predecessor of hull member x on this lane's merged line hull;
+// nem = bit mask of segments holding members.
+__device__ __forceinline__ int band_next(const BandSmem& sm, int lg, int SEGW, int lane,
+                                         uint32_t nem, int x)
 {
-    const int L = x >> (31 - __clz(S));
-    const int y = next_in_lane(hb, L, S, SW, x);
+    const int s = x >> lg;
+    const int y = seg_next(sm.hb, s, lg, SEGW, lane, x);
     if (y >= 0) return y;
-    const uint32_t later = (L >= 31) ? 0u : (nonempty & (0xFFFFFFFEu << L));
-    return later ? lo[__ffs(later) - 1] : -1;
+    const uint32_t later = (s >= 31) ? 0u : (nem & (0xFFFFFFFEu << s));
+    return later ? sm.lo[(__ffs(later) - 1) * 32 + lane] : -1;
 }
-__device__ __forceinline__ int hull_prev(const uint32_t* hb, const int* hi,
-                                         uint32_t nonempty, int S, int x)
+__device__ __forceinline__ int band_prev(const BandSmem& sm, int lg, int SEGW, int lane,
+                                         uint32_t nem, int x)
 {
-    const int L = x >> (31 - __clz(S));
-    const int y = prev_in_lane(hb, L, S, x);
+    const int s = x >> lg;
+    const int y = seg_prev(sm.hb, s, lg, SEGW, lane, x);
     if (y >= 0) return y;
-    const uint32_t earlier = nonempty & ((1u << L) - 1u);
-    return earlier ? hi[31 - __clz(earlier)] : -1;
+    const uint32_t earlier = nem & ((1u << s) - 1u);
+    return earlier ? sm.hi[(31 - __clz(earlier)) * 32 + lane] : -1;
 }
 
-// The whole per-line computation, executed by all 32 lanes of a warp.
-//
-// Line must provide:
-//   int  n;                                 line length
-//   bool eval(int k, int& f) const;         f(k) if finite (false = infinite)
-//   int  c(int k) const;                    f(k) + k*k for a finite member
-//   int  feature(int k) const;              output feature of source column k
-// Out must provide:
-//   void store(int j, int value, int feature) const;  value INT32_MAX and
-//        feature -1 when the line has no finite value at all.
-template <class Line, class Out>
-__device__ void warp_envelope(const Line& line, const Out& out, const WarpSmem& sm)
+// The whole per-block computation, called by every thread of the block
+// (blockDim.x = 32 * NW).  Line (per lane) must provide
+//   bool eval(int k, int& f) const   f(k) of this lane's line, false = infinite
+//   int  c(int k) const              f(k) + k*k for a finite position
+//   int  feature(int k) const        output feature of position k
+// and Out either (TILED) store(int line_lane, int j, int v, int f), called by
+// any lane of the segment's warp, or (!TILED) the same called by the line's
+// own lane.  v = INT32_MAX, f = -1 where the line has no finite value.
+template <bool TILED, class Line, class Out>
+__device__ void band_envelope(const Line& line, const Out& out, const BandSmem& sm, int n,
+                              int lg, int NW)
 {
+    const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int n = line.n;
-    const int S = seg_len(n);
-    const int SW = (S + 31) / 32;
-    const int s0 = lane * S;
-    const int s1 = min(s0 + S, n);
-    for (int w = 0; w < SW; ++w) sm.hb[w * 32 + lane] = 0u;
+    const int SEGW = (1 << lg) >> 5;
+    const int s0 = warp << lg;
+    const int s1 = min(s0 + (1 << lg), n);
+    uint32_t* hbw = sm.hb + (size_t)warp * SEGW * 32 + lane;
+    for (int w = 0; w < SEGW; ++w) hbw[w * 32] = 0u;
 
-    // (1) hull of the lane's own segment (stack algorithm of Sec. 3.3.1)
+    // (1) hull of this segment of this lane's line
     int top = -1, sec = -1, ctop = 0, csec = 0, first = -1;
     for (int k = s0; k < s1; ++k) {
         int fk;
@@ -283,43 +289,42 @@ __device__ void warp_envelope(const Line& line, const Out& out, const WarpSmem& 
         const int ck = fk + k * k;
         while (sec >= 0 && hidden(sec, csec, top, ctop, k, ck)) {
             const int off = top - s0;
-            sm.hb[(off >> 5) * 32 + lane] &= ~(1u << (off & 31));
+            hbw[(off >> 5) * 32] &= ~(1u << (off & 31));
             top = sec;
             ctop = csec;
-            sec = prev_in_lane(sm.hb, lane, S, top);
+            sec = seg_prev(sm.hb, warp, lg, SEGW, lane, top);
             if (sec >= 0) csec = line.c(sec);
         }
         const int off = k - s0;
-        sm.hb[(off >> 5) * 32 + lane] |= 1u << (off & 31);
+        hbw[(off >> 5) * 32] |= 1u << (off & 31);
         if (first < 0) first = k;
         sec = top;
         csec = ctop;
         top = k;
         ctop = ck;
     }
-    sm.lo[lane] = first;
-    sm.hi[lane] = top;
-    __syncwarp();
+    sm.lo[warp * 32 + lane] = first;
+    sm.hi[warp * 32 + lane] = top;
+    __syncthreads();
 
-    // (2) merge neighbouring hulls, 1+1, 2+2, ..., 16+16 lanes
-#pragma unroll 1
-    for (int half = 1; half < 32; half <<= 1) {
-        if ((lane & (2 * half - 1)) == 0)
-            bridge(line, sm.hb, sm.lo, sm.hi, S, SW, lane, lane + half, lane + 2 * half);
-        __syncwarp();
+    // (2) merge segments 1+1, 2+2, ...
+    for (int half = 1; half < NW; half <<= 1) {
+        if ((warp & (2 * half - 1)) == 0 && warp + half < NW)
+            band_bridge(line, sm, lg, SEGW, lane, warp, warp + half, min(warp + 2 * half, NW));
+        __syncthreads();
     }
 
-    // (3) fill this lane's columns
-    const uint32_t nonempty = __ballot_sync(FULL, sm.lo[lane] >= 0);
+    // (3) fill
+    uint32_t nem = 0;
+    for (int w = 0; w < NW; ++w) nem |= (uint32_t)(sm.lo[w * 32 + lane] >= 0) << w;
     int cur = -1, fcur = 0, featcur = -1, nxt = -1, fnxt = 0;
-    bool feat_stale = false;
-    if (nonempty && s0 < s1) {
-        const uint32_t before = nonempty & ((1u << lane) - 1u);
-        cur = before ? sm.hi[31 - __clz(before)] : sm.lo[__ffs(nonempty) - 1];
+    bool stale = false;
+    if (nem && s0 < s1) {
+        const uint32_t before = nem & ((1u << warp) - 1u);
+        cur = before ? sm.hi[(31 - __clz(before)) * 32 + lane] : sm.lo[(__ffs(nem) - 1) * 32 + lane];
         line.eval(cur, fcur);
-        // walk left while strictly better at s0
-        for (;;) {
-            const int p = hull_prev(sm.hb, sm.hi, nonempty, S, cur);
+        for (;;) {  // walk left while strictly better at s0
+            const int p = band_prev(sm, lg, SEGW, lane, nem, cur);
             if (p < 0) break;
             int fp;
             line.eval(p, fp);
@@ -331,51 +336,59 @@ __device__ void warp_envelope(const Line& line, const Out& out, const WarpSmem& 
                 break;
             }
         }
-        nxt = hull_next(sm.hb, sm.lo, nonempty, S, SW, cur);
+        nxt = band_next(sm, lg, SEGW, lane, nem, cur);
         if (nxt >= 0) line.eval(nxt, fnxt);
         featcur = line.feature(cur);
     }
-
-    const int nch = S / OUT_CHUNK;
-    for (int q = 0; q < nch; ++q) {
-        int v[OUT_CHUNK], ft[OUT_CHUNK];
+    const int nq = ((1 << lg) + OC - 1) / OC;
+    for (int q = 0; q < nq; ++q) {
+        int v[OC], ft[OC];
 #pragma unroll
-        for (int t = 0; t < OUT_CHUNK; ++t) {
-            const int j = s0 + q * OUT_CHUNK + t;
+        for (int t = 0; t < OC; ++t) {
+            const int j = s0 + q * OC + t;
             v[t] = INT32_MAX;
             ft[t] = -1;
             if (j < s1 && cur >= 0) {
                 while (nxt >= 0 && fnxt + (j - nxt) * (j - nxt) <= fcur + (j - cur) * (j - cur)) {
                     cur = nxt;
                     fcur = fnxt;
-                    feat_stale = true;
-                    nxt = hull_next(sm.hb, sm.lo, nonempty, S, SW, cur);
+                    stale = true;
+                    nxt = band_next(sm, lg, SEGW, lane, nem, cur);
                     if (nxt >= 0) line.eval(nxt, fnxt);
                 }
-                if (feat_stale) {
+                if (stale) {
                     featcur = line.feature(cur);
-                    feat_stale = false;
+                    stale = false;
                 }
                 v[t] = fcur + (j - cur) * (j - cur);
                 ft[t] = featcur;
             }
         }
-        int4* td = reinterpret_cast<int4*>(sm.tileD + lane * OUT_CHUNK);
-        int4* tf = reinterpret_cast<int4*>(sm.tileF + lane * OUT_CHUNK);
-        td[0] = make_int4(v[0], v[1], v[2], v[3]);
-        td[1] = make_int4(v[4], v[5], v[6], v[7]);
-        tf[0] = make_int4(ft[0], ft[1], ft[2], ft[3]);
-        tf[1] = make_int4(ft[4], ft[5], ft[6], ft[7]);
-        __syncwarp();
+        if (TILED) {
+            int4* td = reinterpret_cast<int4*>(sm.tileD + (warp * 32 + lane) * OC);
+            int4* tf = reinterpret_cast<int4*>(sm.tileF + (warp * 32 + lane) * OC);
+            td[0] = make_int4(v[0], v[1], v[2], v[3]);
+            td[1] = make_int4(v[4], v[5], v[6], v[7]);
+            tf[0] = make_int4(ft[0], ft[1], ft[2], ft[3]);
+            tf[1] = make_int4(ft[4], ft[5], ft[6], ft[7]);
+            __syncwarp();
+            const int* tD = sm.tileD + warp * 32 * OC;
+            const int* tF = sm.tileF + warp * 32 * OC;
 #pragma unroll
-        for (int p = 0; p < 32 / (32 / OUT_CHUNK); ++p) {
-            const int L = p * (32 / OUT_CHUNK) + lane / OUT_CHUNK;
-            const int t = lane % OUT_CHUNK;
-            const int j = L * S + q * OUT_CHUNK + t;
-            if (j < min(L * S + S, n))
-                out.store(j, sm.tileD[L * OUT_CHUNK + t], sm.tileF[L * OUT_CHUNK + t]);
+            for (int p = 0; p < OC; ++p) {
+                const int ln = p * (32 / OC) + lane / OC;
+                const int t = lane % OC;
+                const int j = s0 + q * OC + t;
+                if (j < s1) out.store(ln, j, tD[ln * OC + t], tF[ln * OC + t]);
+            }
+            __syncwarp();
+        } else {
+#pragma unroll
+            for (int t = 0; t < OC; ++t) {
+                const int j = s0 + q * OC + t;
+                if (j < s1) out.store(lane, j, v[t], ft[t]);
+            }
         }
-        __syncwarp();
     }
 }
 

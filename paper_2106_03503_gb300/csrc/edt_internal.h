@@ -69,6 +69,24 @@ cudaError_t launch_batch(const BatchJobDev* jobs_dev, int njobs,
                          int64_t k1_warps, int64_t k2_blocks, int max_W,
                          void* scratch_base, cudaStream_t stream);
 
+// Kernel tracing (see edt_trace_enable): trace_begin records the start event
+// of a launch on `stream` and returns a slot, trace_end its stop event.
+bool trace_on();
+int trace_begin(const char* kernel, cudaStream_t stream);
+void trace_end(int slot, cudaStream_t stream);
+
+// Enqueue `launch` (a callable returning cudaError_t) bracketed by trace
+// events when tracing is on.
+template <class F>
+cudaError_t traced(const char* kernel, cudaStream_t stream, F&& launch)
+{
+    if (!trace_on()) return launch();
+    const int slot = trace_begin(kernel, stream);
+    const cudaError_t e = launch();
+    trace_end(slot, stream);
+    return e;
+}
+
 cudaError_t set_2d_attributes();
 cudaError_t set_3d_attributes();
 

@@ -2,89 +2,104 @@
 // Transform and its Computation": lower envelope of the parabolas of Eq. (5)
 // per row), fused with the end of the column pass and the optional sqrt.
 //
-// One block handles rows of one band of 32 rows over the full width W.  Its
-// prologue stages, per column, the band's source-bit word and the nearest
-// source rows above and below the band (8 bytes per column, from the column
-// pass scratch) in shared memory.  For any row of the band the nearest source
-// row g of column k then follows from a few bit operations (highest set bit at
-// or above the row, lowest at or below), i.e. the squared vertical distance
-// D_v(k) = (i - g)^2 of Fig. 18(b) is rebuilt on demand and never stored.
-// Each warp then runs the lower-envelope engine on one row at a time and
-// writes D, F (= g * W + k of the owning parabola) and optionally sqrt(D).
+// One block handles one band of 32 rows over the full width W: lane l of
+// every warp works on row 32*band + l, and the warps split the columns into
+// segments (band engine, edt_engine.cuh).  The prologue stages, per column,
+// the band's source-bit word and the nearest source rows above and below the
+// band (8 bytes per column, from the column-pass scratch) in shared memory.
+// For row i the nearest source row g of column k then follows from a few bit
+// operations (highest set bit at or above the row, lowest at or below), i.e.
+// the squared vertical distance D_v(k) = (i - g)^2 of Fig. 18(b) is rebuilt on
+// demand and never stored; all 32 rows read the same column word at once.
 #include "edt_engine.cuh"
 #include "edt_internal.h"
 
 namespace edt {
 
-struct Row2D {
-    int n;                       // W
-    const uint32_t* bits;        // padded [W]: source bits of the band
-    const uint32_t* updn;        // padded [W]: nearest source above | below << 16
-    int lg;                      // log2 of the lane segment length
-    int base;                    // first row of the band
-    int r;                       // row within the band
-    int W;
+// Encoded nearest source rows outside the band: up as int16 (-32768 = none),
+// dn as uint16 (65535 = none), so that i - up and dn - i exceed any real
+// distance (< 32768) when there is no source on that side.
+constexpr uint32_t UP_NONE = 0x8000u;
+constexpr uint32_t DN_NONE = 0xFFFFu;
 
-    __device__ __forceinline__ int nearest(int k) const
+struct BandRow2D {
+    const uint32_t* bits;   // [W]: source bits of the band's 32 rows
+    const uint32_t* updn;   // [W]: encoded up | dn << 16
+    int base;               // first row of the band
+    int i;                  // this lane's row
+    int W;
+    uint32_t mle, mge;      // bits at / above and at / below this row
+    bool valid;
+
+    __device__ __forceinline__ bool parts(int k, int& up, int& dn) const
     {
-        const int idx = pad_index(k, lg);
-        const uint32_t ud = updn[idx];
-        return nearest_in_column(bits[idx], base, r, (int)(ud & 0xFFFFu), (int)(ud >> 16));
+        const uint32_t w = bits[k];
+        const uint32_t ud = updn[k];
+        const uint32_t a = w & mle, b = w & mge;
+        up = a ? base + 31 - __clz(a) : (int)(short)(ud & 0xFFFFu);
+        dn = b ? base + __ffs(b) - 1 : (int)(ud >> 16);
+        return valid;
     }
     __device__ __forceinline__ bool eval(int k, int& f) const
     {
-        const int g = nearest(k);
-        if (g < 0) return false;
-        const int d = base + r - g;
+        int up, dn;
+        if (!parts(k, up, dn)) return false;
+        const int d = min(i - up, dn - i);
+        if (d >= 32768) return false;
         f = d * d;
         return true;
     }
     __device__ __forceinline__ int c(int k) const
     {
-        const int d = base + r - nearest(k);
+        int up, dn;
+        parts(k, up, dn);
+        const int d = min(i - up, dn - i);
         return d * d + k * k;
     }
-    __device__ __forceinline__ int feature(int k) const { return nearest(k) * W + k; }
+    __device__ __forceinline__ int feature(int k) const
+    {
+        int up, dn;
+        parts(k, up, dn);
+        return ((i - up <= dn - i) ? up : dn) * W + k;
+    }
 };
 
-struct Out2D {
+struct BandOut2D {
     int32_t* D;
     int32_t* F;
     float* dist;
-    int64_t rowoff;
-    __device__ __forceinline__ void store(int j, int v, int f) const
+    int base, H, W;
+    __device__ __forceinline__ void store(int ln, int j, int v, int f) const
     {
-        const int64_t i = rowoff + j;
-        if (D) D[i] = v;
-        if (F) F[i] = f;
-        if (dist) dist[i] = sqrt_rn_int(v);
+        const int row = base + ln;
+        if (row >= H) return;
+        const int64_t idx = (int64_t)row * W + j;
+        if (D) D[idx] = v;
+        if (F) F[idx] = f;
+        if (dist) dist[idx] = sqrt_rn_int(v);
     }
 };
 
-__global__ void __launch_bounds__(256)
-k_rows2d(int H, int W, ColScratch s, int rows_per_cta, int cpb, int32_t* D,
-         int32_t* F, float* dist)
+// Shared memory of one band block: column data + band engine.
+static size_t band2d_smem(int W, int lg, int NW)
+{
+    return (((size_t)8 * W + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5, true);
+}
+
+__global__ void __launch_bounds__(1024)
+k_rows2d(int H, int W, ColScratch s, int lg, int NW, int32_t* D, int32_t* F, float* dist)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lg = seg_log2(W);
-    const int S = 1 << lg;
-    const int SW = (S + 31) / 32;
-    const int np = padded_len(W);
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     uint32_t* sbits = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* supdn = sbits + np;
-    const int col_bytes = ((2 * np * 4) + 15) & ~15;
-    const WarpSmem sm = carve_warp_smem(smem + col_bytes + warp * warp_smem_bytes(SW), SW);
-
-    const int b = blockIdx.x / cpb;
-    const int chunk = blockIdx.x % cpb;
+    uint32_t* supdn = sbits + W;
+    const BandSmem sm = carve_band_smem(smem + (((size_t)8 * W + 15) & ~size_t(15)), NW,
+                                        (1 << lg) >> 5, true);
+    const int b = blockIdx.x;
     const int G = b >> 5;
     const uint32_t* Cb = s.C + (int64_t)b * W;
     const uint32_t* Ub = s.U + (int64_t)b * W;
     const uint32_t* GABg = s.GAB + (int64_t)G * W;
     for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        const uint32_t w = Cb[j];
         const uint32_t u = Ub[j];
         uint32_t up = u & 0xFFFFu, dn = u >> 16;
         if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
@@ -92,37 +107,38 @@ k_rows2d(int H, int W, ColScratch s, int rows_per_cta, int cpb, int32_t* D,
             if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
             if (dn == (uint32_t)NONE16) dn = gab >> 16;
         }
-        const int idx = pad_index(j, lg);
-        sbits[idx] = w;
-        supdn[idx] = up | (dn << 16);
+        sbits[j] = Cb[j];
+        supdn[j] = (up == (uint32_t)NONE16 ? UP_NONE : up) | ((dn == (uint32_t)NONE16 ? DN_NONE : dn) << 16);
     }
     __syncthreads();
 
-    const int rbeg = chunk * rows_per_cta;
-    const int rend = min(rbeg + rows_per_cta, min(32, H - b * 32));
-    for (int r = rbeg + warp; r < rend; r += nwarps) {
-        const Row2D line{W, sbits, supdn, lg, b * 32, r, W};
-        const Out2D out{D, F, dist, (int64_t)(b * 32 + r) * W};
-        warp_envelope(line, out, sm);
-        __syncwarp();
-    }
+    const int lane = threadIdx.x & 31;
+    BandRow2D line;
+    line.bits = sbits;
+    line.updn = supdn;
+    line.base = b * 32;
+    line.i = b * 32 + lane;
+    line.W = W;
+    line.mle = FULL >> (31 - lane);
+    line.mge = FULL << lane;
+    line.valid = line.i < H;
+    const BandOut2D out{D, F, dist, b * 32, H, W};
+    band_envelope<true>(line, out, sm, W, lg, NW);
 }
 
 cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
                           int32_t* D, int32_t* F, float* dist, int sm_count,
                           cudaStream_t stream)
 {
-    int cpb = 1;  // blocks per band
-    while (cpb < 8 && (int64_t)g.nb * cpb < 2 * (int64_t)sm_count) cpb *= 2;
-    const int rows_per_cta = 32 / cpb;
-    const int nwarps = rows_per_cta < 8 ? rows_per_cta : 8;
-    const int lg = seg_log2(W);
-    const int SW = ((1 << lg) + 31) / 32;
-    const int np = padded_len(W);
-    const size_t smem = (((size_t)2 * np * 4 + 15) & ~size_t(15)) +
-                        (size_t)nwarps * warp_smem_bytes(SW);
-    const unsigned blocks = (unsigned)(g.nb * cpb);
-    k_rows2d<<<blocks, nwarps * 32, smem, stream>>>(H, W, s, rows_per_cta, cpb, D, F, dist);
+    (void)sm_count;
+    int max_nw = 32, lg = 0, NW = 0;
+    for (; max_nw >= 1; max_nw >>= 1) {
+        lg = band_seg_log2(W, max_nw);
+        NW = (W + (1 << lg) - 1) >> lg;
+        if (band2d_smem(W, lg, NW) <= 227 * 1024) break;
+    }
+    const size_t smem = band2d_smem(W, lg, NW);
+    k_rows2d<<<(unsigned)g.nb, NW * 32, smem, stream>>>(H, W, s, lg, NW, D, F, dist);
     return cudaGetLastError();
 }
 

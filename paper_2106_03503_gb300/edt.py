@@ -55,6 +55,11 @@ _lib.edt_sq2d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _v
 _lib.edt_sq3d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
 _lib.edt_feature.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.edt_feature_host.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.edt_trace_enable.argtypes = [ctypes.c_int]
+_lib.edt_trace_enable.restype = ctypes.c_int
+_lib.edt_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_int64)]
+_lib.edt_trace_read.restype = ctypes.c_int
 _lib.edt_last_error.restype = ctypes.c_char_p
 _lib.edt_version.restype = ctypes.c_char_p
 for _name in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host"):
@@ -62,7 +67,21 @@ for _name in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host"):
 
 EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host", "edt_plan_create",
            "edt_plan_destroy", "edt_batch", "edt_serve_create", "edt_serve_submit",
-           "edt_serve_poll", "edt_serve_destroy", "edt_last_error", "edt_version")
+           "edt_serve_poll", "edt_serve_destroy", "edt_trace_enable", "edt_trace_read",
+           "edt_last_error", "edt_version")
+
+
+def trace_enable(on: bool = True):
+    """Start (and reset) or stop per-kernel event timing inside libedt."""
+    _check(_lib.edt_trace_enable(1 if on else 0))
+
+
+def trace_read(kernel: str):
+    """(total milliseconds, launches) of `kernel` since tracing was enabled."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(_lib.edt_trace_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def version() -> str:

@@ -151,6 +151,25 @@ edt_status edt_trace_enable(int on);
 edt_status edt_trace_read(const char *kernel, double *total_ms,
                           int64_t *launches);
 
+/* Allocation-free variant of edt_feature for 2-D images.  The paper has no
+ * counterpart: this is an interface for callers that may not allocate device
+ * memory on the call path -- plugins whose host framework owns every device
+ * allocation, or latency-critical code that cannot risk the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  It calls no allocator: the
+ * column-pass scratch is a fixed 32 MiB static device array (enough for
+ * 8192 x 8192), reserved on every GPU that loads libedt until the process
+ * exits; images whose scratch does not fit return EDT_ERR_TOO_LARGE.
+ * Arguments as for edt_feature with ndim = 2 (device pointers; F required, D
+ * and dist may be NULL); results are bit-identical to edt_feature.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other threads) race on it, so the caller
+ * must order them (e.g. one stream). */
+edt_status edt_feature2d_noalloc(const uint8_t *mask, int H, int W, int mode,
+                                 int32_t *D, int32_t *F, float *dist,
+                                 edt_stream_t stream);
+
 /* Message of the last failure on the calling thread ("" when none). */
 const char *edt_last_error(void);
 

@@ -105,16 +105,18 @@ typedef struct {
 
 typedef struct edt_plan edt_plan;
 
-/* A batch plan owns the device scratch and the CUDA graph that run up to
- * n_max 2-D jobs in one replay.  `max_pixels` bounds the total pixel count
- * of one batch (scratch is sized from it).  Not thread-safe: one plan per
- * thread / stream. */
+/* A batch plan owns the device scratch, a device job table and the CUDA graph
+ * that run up to n_max 2-D jobs (width <= 2048) in one replay.  `max_pixels`
+ * bounds the total pixel count of one batch (scratch, about 0.26 bytes per
+ * pixel, is sized from it).  Not thread-safe: use one plan from one thread
+ * and one stream; plan creation allocates and may synchronise. */
 edt_status edt_plan_create(edt_plan **plan, int n_max, int64_t max_pixels);
 edt_status edt_plan_destroy(edt_plan *plan);
 
-/* Run n jobs (n <= n_max) as one graph replay on `stream`: the job table is
- * copied to the device and two batched kernels cover every job.  Results are
- * bit-identical to n separate edt_feature calls.  2-D jobs only. */
+/* Run n 2-D jobs (n <= n_max) as one graph replay on `stream`: the job table
+ * is copied to the device and two persistent kernels cover every job (column
+ * pass, then row pass).  Results are bit-identical to n separate edt_feature
+ * calls.  Returns after enqueueing; the host may then reuse `jobs`. */
 edt_status edt_batch(edt_plan *plan, const edt_job *jobs, int n,
                      edt_stream_t stream);
 

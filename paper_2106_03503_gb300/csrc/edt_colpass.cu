@@ -94,18 +94,14 @@ __device__ __forceinline__ uint32_t load_row_bits(const uint8_t* __restrict__ p,
     return bits;
 }
 
+// The work of one warp: columns [32*tile, 32*tile + 32) x bands of group G.
+// cw and upS are this warp's 32 x 32 shared scratch tiles.
 template <bool VEC>
-__global__ void __launch_bounds__(K1_WARPS * 32)
-k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s)
+__device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g, int mode,
+                             const ColScratch& s, int64_t tile, int G,
+                             uint32_t (*cw)[32], uint32_t (*upS)[32])
 {
-    __shared__ uint32_t cw[K1_WARPS][32][32];   // [warp][band][column]
-    __shared__ uint32_t upS[K1_WARPS][32][32];  // forward-scan results
-    const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp;
-    if (gw >= g.ntiles * (int64_t)g.nG) return;  // whole warp; no block sync below
-    const int64_t tile = gw % g.ntiles;
-    const int G = (int)(gw / g.ntiles);
     const int64_t W = g.cols;
     const int64_t col0 = tile * 32;
     const int64_t col = col0 + lane;
@@ -136,7 +132,7 @@ k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s)
                 const uint32_t b = __ballot_sync(FULL, (src[u] >> t) & 1u);
                 if (lane == t) mine = b;
             }
-            cw[warp][bl + u][lane] = mine;
+            cw[bl + u][lane] = mine;
             if (col < W) s.C[(int64_t)(b0 + bl + u) * W + col] = mine;
         }
     }
@@ -146,8 +142,8 @@ k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s)
     if (col < W) {
         int last = NONE16, first = NONE16;
         for (int bl = 0; bl < nbg; ++bl) {
-            const uint32_t w = cw[warp][bl][lane];
-            upS[warp][bl][lane] = (uint32_t)last;
+            const uint32_t w = cw[bl][lane];
+            upS[bl][lane] = (uint32_t)last;
             if (w) {
                 last = (b0 + bl) * 32 + 31 - __clz(w);
                 if (first == NONE16) first = (b0 + bl) * 32 + __ffs(w) - 1;
@@ -155,8 +151,8 @@ k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s)
         }
         int nxt = NONE16;
         for (int bl = nbg - 1; bl >= 0; --bl) {
-            const uint32_t w = cw[warp][bl][lane];
-            s.U[(int64_t)(b0 + bl) * W + col] = upS[warp][bl][lane] | ((uint32_t)nxt << 16);
+            const uint32_t w = cw[bl][lane];
+            s.U[(int64_t)(b0 + bl) * W + col] = upS[bl][lane] | ((uint32_t)nxt << 16);
             if (w) nxt = (b0 + bl) * 32 + __ffs(w) - 1;
         }
         s.GFL[(int64_t)G * W + col] = (uint32_t)first | ((uint32_t)last << 16);
@@ -174,17 +170,75 @@ k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s)
         int above = NONE16;
         for (int G2 = 0; G2 < g.nG; ++G2) {
             const uint32_t v = __ldcg(s.GFL + (int64_t)G2 * W + col);
-            cw[warp][G2][lane] = (uint32_t)above;
+            cw[G2][lane] = (uint32_t)above;
             if ((v >> 16) != (uint32_t)NONE16) above = (int)(v >> 16);
         }
         int below = NONE16;
         for (int G2 = g.nG - 1; G2 >= 0; --G2) {
             const uint32_t v = __ldcg(s.GFL + (int64_t)G2 * W + col);
-            s.GAB[(int64_t)G2 * W + col] = cw[warp][G2][lane] | ((uint32_t)below << 16);
+            s.GAB[(int64_t)G2 * W + col] = cw[G2][lane] | ((uint32_t)below << 16);
             if ((v & 0xFFFFu) != (uint32_t)NONE16) below = (int)(v & 0xFFFFu);
         }
     }
+    __syncwarp();
     if (lane == 0) s.cnt[tile] = 0u;  // ready for the next call
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(K1_WARPS * 32)
+k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s)
+{
+    __shared__ uint32_t cw[K1_WARPS][32][32];   // [warp][band][column]
+    __shared__ uint32_t upS[K1_WARPS][32][32];  // forward-scan results
+    const int warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp;
+    if (gw >= g.ntiles * (int64_t)g.nG) return;  // whole warp; no block sync below
+    colbits_warp<VEC>(mask, g, mode, s, gw % g.ntiles, (int)(gw / g.ntiles), cw[warp], upS[warp]);
+}
+
+// Persistent column pass over every job of a batch: warp units are numbered
+// job by job (k1_first) and handed out in a grid-stride loop.
+__global__ void __launch_bounds__(K1_WARPS * 32)
+k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs)
+{
+    __shared__ uint32_t cw[K1_WARPS][32][32];
+    __shared__ uint32_t upS[K1_WARPS][32][32];
+    const int warp = threadIdx.x >> 5;
+    const int64_t total = hdr->k1_total;
+    const int nj = hdr->njobs;
+    for (int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp; gw < total;
+         gw += (int64_t)gridDim.x * K1_WARPS) {
+        int lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].k1_first <= gw) lo = mid; else hi = mid - 1;
+        }
+        const BatchJob& J = jobs[lo];
+        const ColGeom g = J.g;
+        const ColScratch s = J.s;
+        const int64_t local = gw - J.k1_first;
+        if (J.vec)
+            colbits_warp<true>(J.mask, g, J.mode, s, local % g.ntiles, (int)(local / g.ntiles), cw[warp], upS[warp]);
+        else
+            colbits_warp<false>(J.mask, g, J.mode, s, local % g.ntiles, (int)(local / g.ntiles), cw[warp], upS[warp]);
+        __syncwarp();
+    }
+}
+
+int batch_colbits_blocks_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_colbits, K1_WARPS * 32, 0) !=
+            cudaSuccess || n < 1)
+        n = 1;
+    return n;
+}
+
+cudaError_t launch_batch_colbits(const BatchHeader* hdr, const BatchJob* jobs, int blocks,
+                                 cudaStream_t stream)
+{
+    k_batch_colbits<<<blocks, K1_WARPS * 32, 0, stream>>>(hdr, jobs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_colbits(const uint8_t* mask, const ColGeom& g, int mode,

@@ -269,11 +269,24 @@ __device__ __forceinline__ int band_prev(const BandSmem& sm, int lg, int SEGW, i
 // and Out either (TILED) store(int line_lane, int j, int v, int f), called by
 // any lane of the segment's warp, or (!TILED) the same called by the line's
 // own lane.  v = INT32_MAX, f = -1 where the line has no finite value.
-template <bool TILED, class Line, class Out>
+// Barrier of the NW warps that share one band engine: the whole block, or a
+// named barrier when a block runs several engines side by side.
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {
+    int id, nthreads;
+    __device__ __forceinline__ void operator()() const
+    {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+    }
+};
+
+template <bool TILED, class Line, class Out, class Sync = BlockSync>
 __device__ void band_envelope(const Line& line, const Out& out, const BandSmem& sm, int n,
-                              int lg, int NW)
+                              int lg, int NW, int warp = -1, Sync sync = Sync())
 {
-    const int warp = threadIdx.x >> 5;
+    if (warp < 0) warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int SEGW = (1 << lg) >> 5;
     const int s0 = warp << lg;
@@ -305,13 +318,13 @@ __device__ void band_envelope(const Line& line, const Out& out, const BandSmem& 
     }
     sm.lo[warp * 32 + lane] = first;
     sm.hi[warp * 32 + lane] = top;
-    __syncthreads();
+    sync();
 
     // (2) merge segments 1+1, 2+2, ...
     for (int half = 1; half < NW; half <<= 1) {
         if ((warp & (2 * half - 1)) == 0 && warp + half < NW)
             band_bridge(line, sm, lg, SEGW, lane, warp, warp + half, min(warp + 2 * half, NW));
-        __syncthreads();
+        sync();
     }
 
     // (3) fill

@@ -50,24 +50,43 @@ cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
 cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,
                            int32_t* F, float* dist, cudaStream_t stream);
 
-// Batched 2-D transforms (all jobs of a plan in two launches).
-struct BatchJobDev {
+// Batched 2-D transforms.  A device job table (header + jobs) drives two
+// persistent kernels: the column pass over every job's (tile, group) warps and
+// the row pass over every job's work items (`groups` bands per item, several
+// bands of a narrow image side by side in one block).
+struct BatchJob {
     const uint8_t* mask;
     int32_t* D;
     int32_t* F;
     float* dist;
-    int H, W, mode, nb, nG;
-    int64_t ntiles;
-    int64_t scratch_off;   // byte offset of this job's ColScratch
-    int64_t k1_first;      // first K1 warp index of this job
-    int64_t k2_first;      // first K2 block index of this job
-    int k2_rows;           // rows per K2 block
-    int pad_;
+    ColScratch s;
+    ColGeom g;             // rows = H, cols = W
+    int mode, vec;         // vec: 16-byte mask loads allowed
+    int lg, NW, groups;    // row pass: segment log2, warps per band, bands per item
+    int pad0;
+    int64_t k1_first;      // first column-pass warp of this job
+    int64_t k2_first;      // first row-pass work item of this job
 };
 
-cudaError_t launch_batch(const BatchJobDev* jobs_dev, int njobs,
-                         int64_t k1_warps, int64_t k2_blocks, int max_W,
-                         void* scratch_base, cudaStream_t stream);
+struct BatchHeader {
+    int njobs;
+    int pad0;
+    int64_t k1_total;
+    int64_t k2_total;
+};
+
+constexpr int BATCH_MAX_W = 2048;      // widest image a batch accepts
+constexpr int BATCH_K2_WARPS = 16;     // threads per row-pass block / 32
+int batch_colbits_blocks_per_sm();
+int batch_rows_blocks_per_sm();
+
+void batch_row_geometry(int W, int& lg, int& NW, int& groups);
+size_t batch_rows_smem();
+cudaError_t launch_batch_colbits(const BatchHeader* hdr, const BatchJob* jobs, int blocks,
+                                 cudaStream_t stream);
+cudaError_t launch_batch_rows2d(const BatchHeader* hdr, const BatchJob* jobs, unsigned* work,
+                                int blocks, cudaStream_t stream);
+cudaError_t set_batch_attributes();
 
 // Kernel tracing (see edt_trace_enable): trace_begin records the start event
 // of a launch on `stream` and returns a slot, trace_end its stop event.

@@ -142,6 +142,130 @@ cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
     return cudaGetLastError();
 }
 
+// --- batched row pass -------------------------------------------------------
+
+// Row-pass geometry of a batch job of width W: segments of 2^lg columns, NW
+// warps per band, `groups` bands side by side in one 16-warp block.
+void batch_row_geometry(int W, int& lg, int& NW, int& groups)
+{
+    lg = band_seg_log2(W, BATCH_K2_WARPS);
+    NW = (W + (1 << lg) - 1) >> lg;
+    groups = BATCH_K2_WARPS / NW;
+}
+
+__host__ __device__ static size_t batch_group_bytes(int W, int lg, int NW)
+{
+    return (((size_t)8 * W + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5, true);
+}
+
+size_t batch_rows_smem()
+{
+    size_t mx = 0;
+    for (int W = 1; W <= BATCH_MAX_W; ++W) {
+        int lg, NW, groups;
+        batch_row_geometry(W, lg, NW, groups);
+        const size_t b = (size_t)groups * batch_group_bytes(W, lg, NW);
+        if (b > mx) mx = b;
+    }
+    return mx;
+}
+
+// Barrier of one band engine inside a block that runs several: a warp barrier
+// for one-warp engines, else a named barrier (ids 1..8; 0 is __syncthreads).
+struct DynSync {
+    int id, nthreads;
+    __device__ __forceinline__ void operator()() const
+    {
+        if (nthreads <= 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+    }
+};
+
+__global__ void __launch_bounds__(BATCH_K2_WARPS * 32, 2)
+k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs,
+               unsigned* __restrict__ work)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = hdr->k2_total;
+    const int nj = hdr->njobs;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(work, 1u);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].k2_first <= item) lo = mid; else hi = mid - 1;
+        }
+        const BatchJob& J = jobs[lo];
+        const int W = (int)J.g.cols, H = J.g.rows, lg = J.lg, NW = J.NW;
+        const int grp = warp / NW, wg = warp - grp * NW;
+        const int b = (int)((item - J.k2_first) * J.groups) + grp;
+        if (grp < J.groups && b < J.g.nb) {
+            unsigned char* base = smem + (size_t)grp * batch_group_bytes(W, lg, NW);
+            uint32_t* sbits = reinterpret_cast<uint32_t*>(base);
+            uint32_t* supdn = sbits + W;
+            const BandSmem sm = carve_band_smem(base + (((size_t)8 * W + 15) & ~size_t(15)), NW,
+                                                (1 << lg) >> 5, true);
+            const DynSync sync{1 + grp, NW * 32};
+            const uint32_t* Cb = J.s.C + (int64_t)b * W;
+            const uint32_t* Ub = J.s.U + (int64_t)b * W;
+            const uint32_t* GABg = J.s.GAB + (int64_t)(b >> 5) * W;
+            for (int j = wg * 32 + lane; j < W; j += NW * 32) {
+                const uint32_t u = Ub[j];
+                uint32_t up = u & 0xFFFFu, dn = u >> 16;
+                if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
+                    const uint32_t gab = GABg[j];
+                    if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
+                    if (dn == (uint32_t)NONE16) dn = gab >> 16;
+                }
+                sbits[j] = Cb[j];
+                supdn[j] = (up == (uint32_t)NONE16 ? UP_NONE : up) |
+                           ((dn == (uint32_t)NONE16 ? DN_NONE : dn) << 16);
+            }
+            sync();
+            BandRow2D line;
+            line.bits = sbits;
+            line.updn = supdn;
+            line.base = b * 32;
+            line.i = b * 32 + lane;
+            line.W = W;
+            line.mle = FULL >> (31 - lane);
+            line.mge = FULL << lane;
+            line.valid = line.i < H;
+            const BandOut2D out{J.D, J.F, J.dist, b * 32, H, W};
+            band_envelope<true>(line, out, sm, W, lg, NW, wg, sync);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_batch_rows2d(const BatchHeader* hdr, const BatchJob* jobs, unsigned* work,
+                                int blocks, cudaStream_t stream)
+{
+    k_batch_rows2d<<<blocks, BATCH_K2_WARPS * 32, batch_rows_smem(), stream>>>(hdr, jobs, work);
+    return cudaGetLastError();
+}
+
+cudaError_t set_batch_attributes()
+{
+    return cudaFuncSetAttribute(k_batch_rows2d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)batch_rows_smem());
+}
+
+int batch_rows_blocks_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows2d, BATCH_K2_WARPS * 32,
+                                                      batch_rows_smem()) != cudaSuccess || n < 1)
+        n = 1;
+    return n;
+}
+
 cudaError_t set_2d_attributes()
 {
     return cudaFuncSetAttribute(k_rows2d, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

@@ -84,6 +84,75 @@ def trace_read(kernel: str):
     return ms.value, n.value
 
 
+_lib.edt_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64]
+_lib.edt_plan_create.restype = ctypes.c_int
+_lib.edt_plan_destroy.argtypes = [ctypes.c_void_p]
+_lib.edt_plan_destroy.restype = ctypes.c_int
+_lib.edt_batch.argtypes = [ctypes.c_void_p, ctypes.POINTER(Job), ctypes.c_int, _vp]
+_lib.edt_batch.restype = ctypes.c_int
+
+
+def _job(mask, mode, D, F, dist):
+    j = Job()
+    j.mask = mask.data_ptr()
+    j.ndim = mask.dim()
+    for a in range(3):
+        j.shape[a] = int(mask.shape[a]) if a < mask.dim() else 0
+    j.mode = int(mode)
+    j.D = None if D is None else D.data_ptr()
+    j.F = F.data_ptr()
+    j.dist = None if dist is None else dist.data_ptr()
+    return j
+
+
+class Plan:
+    """A batch plan (edt_plan_create): runs up to n_max 2-D jobs of at most
+    max_pixels pixels in total as one CUDA-graph replay."""
+
+    def __init__(self, n_max: int, max_pixels: int):
+        self._p = ctypes.c_void_p()
+        _check(_lib.edt_plan_create(ctypes.byref(self._p), int(n_max), int(max_pixels)))
+        self._keep = None
+
+    def run(self, jobs, stream=None):
+        """jobs: sequence of (mask, mode, D, F, dist) CUDA tensors (D, dist may
+        be None).  Enqueues the batch on `stream`."""
+        arr = (Job * len(jobs))(*[_job(*j) for j in jobs])
+        self._keep = (arr, jobs)
+        _check(_lib.edt_batch(self._p, arr, len(jobs), _stream_handle(stream)))
+
+    def close(self):
+        if self._p:
+            _check(_lib.edt_plan_destroy(self._p))
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch(masks, mode: int = TO_OBJECT, want_dist: bool = False, plan: Plan = None, stream=None):
+    """Transform a list of 2-D CUDA uint8 masks in one batch; returns a list of
+    (D, F[, dist]) tuples."""
+    masks = [_mask_arg(m) for m in masks]
+    outs = []
+    for m in masks:
+        D = torch.empty(m.shape, dtype=torch.int32, device=m.device)
+        F = torch.empty(m.shape, dtype=torch.int32, device=m.device)
+        dist = torch.empty(m.shape, dtype=torch.float32, device=m.device) if want_dist else None
+        outs.append((D, F, dist))
+    own = plan is None
+    if own:
+        plan = Plan(len(masks), sum(m.numel() for m in masks))
+    plan.run([(m, mode, D, F, dist) for m, (D, F, dist) in zip(masks, outs)], stream)
+    if own:
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        plan.close()
+    return [(D, F, dist) if want_dist else (D, F) for D, F, dist in outs]
+
+
 def version() -> str:
     return _lib.edt_version().decode()
 

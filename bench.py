@@ -145,6 +145,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max_fn(dist_mod, world, device):
+    """max over ranks of a float (identity for one rank); the tensor lives on
+    `device` (the GPU for NCCL, the CPU for gloo)."""
+    def reduce_max(x):
+        if world <= 1:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+        return float(t.item())
+    return reduce_max
+
+
+def whole_job_rate(total_ms_local, px_per_step, steps, world, reduce_max):
+    """Gpixel/s of all ranks' pixels over the slowest rank's timed milliseconds."""
+    total_ms = reduce_max(total_ms_local)
+    return px_per_step * steps * world / (total_ms / 1e3) / 1e9, total_ms
+
+
 def cpu_oracle_rate(mask, repeats=1):
     """Gpixel/s of the oracle (single thread) on both transforms of `mask`."""
     import oracle
@@ -253,13 +272,9 @@ def run_gpu(args, rank, world, local_rank):
     k2_ms, k2_n = edt.trace_read("k_rows2d")
     k1_ms, k1_n = edt.trace_read("k_colbits")
     edt.trace_enable(False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    reduce_max = reduce_max_fn(dist, world, dev)
     px_step = 2 * H * W
-    value = px_step * args.steps * world / (total_ms / 1e3) / 1e9
+    value, total_ms = whole_job_rate(sum(step_ms), px_step, args.steps, world, reduce_max)
 
     # end to end through the public host-buffer entry point (pinned memory)
     hmask = torch.from_numpy(mask_np).pin_memory()
@@ -275,13 +290,9 @@ def run_gpu(args, rank, world, local_rank):
         for mode in (0, 1):
             edt.feature_host(hmask, mode, D=hD[mode], F=hF[mode])
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        barrier()
-    e2e_value = px_step * e2e_steps * world / e2e_s / 1e9
+    e2e_value, _ = whole_job_rate(1e3 * (time.perf_counter() - t0), px_step, e2e_steps, world,
+                                  reduce_max)
+    barrier()
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()

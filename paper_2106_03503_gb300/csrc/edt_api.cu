@@ -57,6 +57,13 @@ edt_status device_setup(int* sm_count)
             if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
             if ((e = set_2d_attributes()) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
             if ((e = set_3d_attributes()) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            // keep freed scratch in this process's default pool instead of
+            // returning it to the driver at every synchronisation
+            cudaMemPool_t pool = nullptr;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t keep = UINT64_MAX;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
             d.sm_count = sms;
             d.ready.store(1, std::memory_order_release);
         }

@@ -153,6 +153,65 @@ def batch(masks, mode: int = TO_OBJECT, want_dist: bool = False, plan: Plan = No
     return [(D, F, dist) if want_dist else (D, F) for D, F, dist in outs]
 
 
+_lib.edt_serve_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_int]
+_lib.edt_serve_create.restype = ctypes.c_int
+_lib.edt_serve_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]
+_lib.edt_serve_submit.restype = ctypes.c_int
+_lib.edt_serve_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+_lib.edt_serve_poll.restype = ctypes.c_int
+_lib.edt_serve_destroy.argtypes = [ctypes.c_void_p]
+_lib.edt_serve_destroy.restype = ctypes.c_int
+
+
+class Server:
+    """Continuous-batching server (edt_serve_*).  Jobs are host (ideally
+    pinned) CPU tensors; results land in host tensors owned by the ticket."""
+
+    def __init__(self, budget_bytes: int, n_streams: int = 2):
+        self._s = ctypes.c_void_p()
+        _check(_lib.edt_serve_create(ctypes.byref(self._s), int(budget_bytes), int(n_streams)))
+        self._live = {}
+
+    def submit(self, mask: torch.Tensor, mode: int = TO_OBJECT, want_D: bool = True,
+               want_dist: bool = False, out=None) -> int:
+        m = mask.contiguous()
+        if m.dtype == torch.bool:
+            m = m.view(torch.uint8)
+        pin = m.is_pinned()
+        if out is None:
+            D = torch.empty(m.shape, dtype=torch.int32, pin_memory=pin) if want_D else None
+            F = torch.empty(m.shape, dtype=torch.int32, pin_memory=pin)
+            dist = torch.empty(m.shape, dtype=torch.float32, pin_memory=pin) if want_dist else None
+        else:
+            D, F, dist = out
+        j = _job(m, mode, D, F, dist)
+        t = ctypes.c_uint64()
+        _check(_lib.edt_serve_submit(self._s, ctypes.byref(j), ctypes.byref(t)))
+        self._live[t.value] = (m, D, F, dist)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running; else (latency_s, (D, F, dist))."""
+        lat = ctypes.c_double()
+        st = _lib.edt_serve_poll(self._s, ctypes.c_uint64(ticket), ctypes.byref(lat))
+        if st == EDT_ERR_NOT_READY:
+            return None
+        bufs = self._live.pop(ticket, None)
+        _check(st)
+        return lat.value, bufs[1:]
+
+    def close(self):
+        if self._s:
+            _check(_lib.edt_serve_destroy(self._s))
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def version() -> str:
     return _lib.edt_version().decode()
 

@@ -175,6 +175,123 @@ def cpu_oracle_rate(mask, repeats=1):
     return 2 * mask.size * repeats / dt / 1e9, dt
 
 
+def measure_batch(edt, torch, dev, reps=5):
+    """4096 masks (sides 64..1024, densities log-uniform 0.001..0.1): one
+    edt_batch graph replay vs one edt_feature call per mask, both on one stream,
+    GPU time by CUDA events around the whole batch (L2 not flushed: the batch
+    is 1.2 Gpixel, far larger than L2)."""
+    from paper_2106_03503_gb300 import inputs
+    masks_np = inputs.batch_4096()
+    masks = [torch.from_numpy(m).to(dev) for m in masks_np]
+    outs = [(torch.empty(m.shape, dtype=torch.int32, device=dev),
+             torch.empty(m.shape, dtype=torch.int32, device=dev)) for m in masks]
+    px = sum(m.numel() for m in masks)
+    plan = edt.Plan(len(masks), px)
+    jobs = [(m, 0, D, F, None) for m, (D, F) in zip(masks, outs)]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    def plain():
+        for m, (D, F) in zip(masks, outs):
+            edt.feature(m, 0, out=(D, F, None))
+
+    t_plain = timed(plain)
+    t_batch = timed(lambda: plan.run(jobs))
+    plan.close()
+    return {"workload": "4096 2D masks, H and W uniform in [64, 1024], Bernoulli density "
+                        "log-uniform in [0.001, 0.1] (seed 4), to-object, D+F",
+            "pixels": px, "plain_ms": t_plain, "batched_ms": t_batch,
+            "plain_gpx_s": px / (t_plain / 1e3) / 1e9, "batched_gpx_s": px / (t_batch / 1e3) / 1e9,
+            "speedup": t_plain / t_batch,
+            "plain": "one edt_feature call per mask from Python (ctypes) on one stream"}
+
+
+def measure_serve(edt, torch, n_jobs=600, warm=60, load=0.8, seed=5):
+    """Serving: Poisson arrivals of mixed jobs (80 % 2-D squares of side
+    128..4096 with Bernoulli density log-uniform 0.001..0.1, 20 % 3-D cubes of
+    side 64..256 of smoothed noise), D+F, host buffers, 40 GB budget.  Masks
+    are drawn from a pool of pre-generated masks of that recipe.  Capacity is
+    measured with a burst first; the arrival rate is `load` x capacity."""
+    import numpy as np
+    from paper_2106_03503_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    specs = inputs.serving_jobs(48, seed)
+    pool = [torch.from_numpy(inputs.draw_job(j)).pin_memory() for j in specs]
+    maxn = max(m.numel() for m in pool)
+    depth = 24
+    ring = [(torch.empty(maxn, dtype=torch.int32).pin_memory(),
+             torch.empty(maxn, dtype=torch.int32).pin_memory()) for _ in range(depth)]
+    srv = edt.Server(40 << 30, n_streams=3)
+    free = list(range(depth))
+    busy = {}
+
+    def submit(k):
+        m = pool[k]
+        slot = free.pop()
+        D = ring[slot][0][:m.numel()].view(m.shape)
+        F = ring[slot][1][:m.numel()].view(m.shape)
+        t = srv.submit(m, 0, out=(D, F, None))
+        busy[t] = (slot, m.numel())
+        return t
+
+    def reap(lats):
+        for t in list(busy):
+            r = srv.poll(t)
+            if r is not None:
+                slot, n = busy.pop(t)
+                free.append(slot)
+                lats.append((r[0], n))
+
+    order = rng.integers(0, len(pool), size=n_jobs + warm)
+    # capacity: keep `depth` jobs in flight
+    lats = []
+    t0 = time.perf_counter()
+    i = 0
+    while i < warm or busy:
+        if i < warm and free:
+            submit(int(order[i]))
+            i += 1
+        else:
+            reap(lats)
+    cap = warm / (time.perf_counter() - t0)
+    # Poisson run at load x capacity
+    rate = load * cap
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
+    lats = []
+    start = time.perf_counter()
+    j = 0
+    while j < n_jobs or busy:
+        now = time.perf_counter() - start
+        if j < n_jobs and arrivals[j] <= now and free:
+            submit(int(order[warm + j]))
+            j += 1
+            continue
+        reap(lats)
+    wall = time.perf_counter() - start
+    srv.close()
+    ms = sorted(1e3 * l for l, _ in lats)
+    px = sum(n for _, n in lats)
+    return {"workload": "Poisson stream, 80% 2D side 128-4096 Bernoulli p log-uniform 0.001-0.1, "
+                        "20% 3D side 64-256 smoothed noise; 40 GB budget, 3 streams, host buffers",
+            "jobs": len(lats), "arrival_rate_jobs_s": rate, "capacity_jobs_s": cap,
+            "throughput_gpx_s": px / wall / 1e9, "p50_ms": ms[len(ms) // 2],
+            "p99_ms": ms[min(len(ms) - 1, int(round(0.99 * (len(ms) - 1))))],
+            "note": f"{len(pool)} pre-generated masks reused; at most {depth} jobs in flight"}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle as the measured arm (rank 0 only)."""
     if rank != 0:
@@ -294,6 +411,17 @@ def run_gpu(args, rank, world, local_rank):
                                   reduce_max)
     barrier()
 
+    extras = {}
+    if args.extras and rank == 0:
+        try:
+            extras["batch"] = measure_batch(edt, torch, dev)
+        except Exception as exc:  # report, do not hide
+            extras["batch"] = {"error": repr(exc)}
+        try:
+            extras["serve"] = measure_serve(edt, torch)
+        except Exception as exc:
+            extras["serve"] = {"error": repr(exc)}
+
     if rank == 0:
         peaks, peak_kind = measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -327,6 +455,7 @@ def run_gpu(args, rank, world, local_rank):
                     "api": "edt_feature_host, pinned host buffers"},
             "gpu_launches": k1_n + k2_n,
             "clocks": clocks,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -339,6 +468,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="libedt", choices=["libedt", "reference"])
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the batch and serving measurements")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus --steps steps of the workload only (for ncu)")
     args = ap.parse_args()

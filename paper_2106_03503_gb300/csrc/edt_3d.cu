@@ -39,9 +39,18 @@ struct LineY {
         const int g = gz[k * 32 + lane];
         return (z - g) * (z - g) + k * k;
     }
-    __device__ __forceinline__ int feature(int k) const
+    __device__ __forceinline__ bool eval2(int k, int& f, int& feat) const
     {
-        return (int)(((uint32_t)gz[k * 32 + lane] << 16) | (uint32_t)k);
+        const int g = gz[k * 32 + lane];
+        if (g < 0) return false;
+        f = (z - g) * (z - g);
+        feat = (int)(((uint32_t)g << 16) | (uint32_t)k);
+        return true;
+    }
+    __device__ __forceinline__ bool is_zero(int k) const { return gz[k * 32 + lane] == z; }
+    __device__ __forceinline__ int self_feature(int k) const
+    {
+        return (int)(((uint32_t)z << 16) | (uint32_t)k);
     }
 };
 
@@ -49,16 +58,19 @@ struct OutY {
     uint32_t* P;             // record of voxel (z, y, x0 + lane) at P[y * W]
     int W;
     bool valid;
-    __device__ __forceinline__ void store(int ln, int j, int v, int f) const
+    __device__ __forceinline__ void finish() const {}
+    __device__ __forceinline__ void store(int j0, int cnt, const int* v, const int* f) const
     {
-        (void)ln;
-        if (valid) P[(int64_t)j * W] = (v == INT32_MAX) ? PNONE : (uint32_t)f;
+        if (!valid) return;
+#pragma unroll
+        for (int t = 0; t < OC; ++t)
+            if (t < cnt) P[(int64_t)(j0 + t) * W] = (v[t] == INT32_MAX) ? PNONE : (uint32_t)f[t];
     }
 };
 
 static size_t ypass_smem(int H, int lg, int NW)
 {
-    return (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5, false);
+    return (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
 // One block: one z, 32 consecutive x (one line per lane), warps = y segments.
@@ -68,7 +80,7 @@ k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
     extern __shared__ __align__(16) unsigned char smem[];
     short* gz = reinterpret_cast<short*>(smem);
     const BandSmem sm = carve_band_smem(smem + (((size_t)H * 32 * 2 + 15) & ~size_t(15)), NW,
-                                        (1 << lg) >> 5, false);
+                                        (1 << lg) >> 5);
     const int lane = threadIdx.x & 31;
     const int xtiles = (W + 31) / 32;
     const int z = blockIdx.x / xtiles;
@@ -98,7 +110,7 @@ k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
 
     const LineY line{gz, lane, z};
     const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
-    band_envelope<false>(line, out, sm, H, lg, NW);
+    band_envelope(line, out, sm, H, lg, NW, nullptr);
 }
 
 // --- x pass ----------------------------------------------------------------
@@ -106,6 +118,7 @@ k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
 struct LineX {
     const uint32_t* rec;     // this lane's row of (z', y') records (pitch odd)
     int z, y, H, W;
+    uint32_t self;           // this row's own record, (z << 16) | y
     bool valid;
     __device__ __forceinline__ bool eval(int k, int& f) const
     {
@@ -122,28 +135,18 @@ struct LineX {
         const int dz = z - (int)(p >> 16), dy = y - (int)(p & 0xFFFFu);
         return dz * dz + dy * dy + k * k;
     }
-    __device__ __forceinline__ int feature(int k) const
+    __device__ __forceinline__ bool eval2(int k, int& f, int& feat) const
     {
+        if (!valid) return false;
         const uint32_t p = rec[k];
-        return ((int)(p >> 16) * H + (int)(p & 0xFFFFu)) * W + k;
+        if (p == PNONE) return false;
+        const int zz = (int)(p >> 16), yy = (int)(p & 0xFFFFu);
+        f = (z - zz) * (z - zz) + (y - yy) * (y - yy);
+        feat = (zz * H + yy) * W + k;
+        return true;
     }
-};
-
-struct OutX {
-    int32_t* D;
-    int32_t* F;
-    float* dist;
-    int64_t row0, nrows;
-    int W;
-    __device__ __forceinline__ void store(int ln, int j, int v, int f) const
-    {
-        const int64_t row = row0 + ln;
-        if (row >= nrows) return;
-        const int64_t i = row * W + j;
-        if (D) D[i] = v;
-        if (F) F[i] = f;
-        if (dist) dist[i] = sqrt_rn_int(v);
-    }
+    __device__ __forceinline__ bool is_zero(int k) const { return rec[k] == self; }
+    __device__ __forceinline__ int self_feature(int k) const { return (z * H + y) * W + k; }
 };
 
 static int xpass_pitch(int W) { return W | 1; }
@@ -151,7 +154,7 @@ static int xpass_pitch(int W) { return W | 1; }
 static size_t xpass_smem(int W, int lg, int NW)
 {
     return (((size_t)32 * xpass_pitch(W) * 4 + 15) & ~size_t(15)) +
-           band_smem_bytes(NW, (1 << lg) >> 5, true);
+           band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
 // One block: 32 consecutive rows (z, y) of the volume (one per lane), warps =
@@ -164,7 +167,7 @@ k_xpass3d(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D,
     const int pitch = W | 1;
     uint32_t* rec = reinterpret_cast<uint32_t*>(smem);   // [32][pitch]
     const BandSmem sm = carve_band_smem(smem + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)), NW,
-                                        (1 << lg) >> 5, true);
+                                        (1 << lg) >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t nrows = (int64_t)Dz * H;
     const int64_t row0 = (int64_t)blockIdx.x * 32;
@@ -184,8 +187,10 @@ k_xpass3d(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D,
     line.H = H;
     line.W = W;
     line.valid = row < nrows;
-    const OutX out{D, F, dist, row0, nrows, W};
-    band_envelope<true>(line, out, sm, W, lg, NW);
+    line.self = ((uint32_t)line.z << 16) | (uint32_t)line.y;
+    const bool vec = (W % 4 == 0) && aligned16(D) && aligned16(F) && aligned16(dist);
+    const RowOut out{D, F, dist, row * W, row < nrows, vec};
+    band_envelope(line, out, sm, W, lg, NW, nullptr);
 }
 
 static void pick_band(int n, size_t (*smem_fn)(int, int, int), int& lg, int& NW)

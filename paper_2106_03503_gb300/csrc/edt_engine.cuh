@@ -34,14 +34,15 @@
 //   (3) Each (segment, line) fills its positions: the owner of a position is
 //       the hull member with the smallest value there; owners move right
 //       monotonically with the position, and along the hull the values at a
-//       fixed position are unimodal, so a walk finds them.  Values either go
-//       straight to memory (lines adjacent in memory) or through a 32 x 8
-//       shared tile that turns them into 32-byte row segments (lines are
-//       rows, positions are columns).
+//       fixed position are unimodal, so a walk finds them.  Each lane writes
+//       its values 8 positions at a time: a row line as two 16-byte stores
+//       per array (one whole 32-byte sector), a column line as single stores
+//       that are coalesced across the 32 neighbouring lines.
 #pragma once
 
 #include <cstdint>
 #include <climits>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace edt {
@@ -116,24 +117,19 @@ struct BandSmem {
     uint32_t* hb;   // [NW][SEGW][32] hull bits: segment, word, lane
     int* lo;        // [NW][32] first hull member of (segment, line), -1 none
     int* hi;        // [NW][32] last hull member
-    int* tileD;     // [NW][32][OC] staging of values (tiled output only)
-    int* tileF;     // [NW][32][OC] staging of features
 };
 
-__host__ __device__ inline size_t band_smem_bytes(int NW, int SEGW, bool tiled)
+__host__ __device__ inline size_t band_smem_bytes(int NW, int SEGW)
 {
-    return (size_t)NW * SEGW * 32 * 4 + (size_t)NW * 64 * 4 +
-           (tiled ? (size_t)NW * 32 * OC * 4 * 2 : 0);
+    return (size_t)NW * SEGW * 32 * 4 + (size_t)NW * 64 * 4;
 }
 
-__device__ __forceinline__ BandSmem carve_band_smem(unsigned char* base, int NW, int SEGW, bool tiled)
+__device__ __forceinline__ BandSmem carve_band_smem(unsigned char* base, int NW, int SEGW)
 {
     BandSmem s;
     s.hb = reinterpret_cast<uint32_t*>(base);
     s.lo = reinterpret_cast<int*>(base + (size_t)NW * SEGW * 32 * 4);
     s.hi = s.lo + NW * 32;
-    s.tileD = tiled ? s.hi + NW * 32 : nullptr;
-    s.tileF = tiled ? s.tileD + NW * 32 * OC : nullptr;
     return s;
 }
 
@@ -261,30 +257,172 @@ __device__ __forceinline__ int band_prev(const BandSmem& sm, int lg, int SEGW, i
     return earlier ? sm.hi[(31 - __clz(earlier)) * 32 + lane] : -1;
 }
 
-// The whole per-block computation, called by every thread of the block
-// (blockDim.x = 32 * NW).  Line (per lane) must provide
-//   bool eval(int k, int& f) const   f(k) of this lane's line, false = infinite
-//   int  c(int k) const              f(k) + k*k for a finite position
-//   int  feature(int k) const        output feature of position k
-// and Out either (TILED) store(int line_lane, int j, int v, int f), called by
-// any lane of the segment's warp, or (!TILED) the same called by the line's
-// own lane.  v = INT32_MAX, f = -1 where the line has no finite value.
-// Barrier of the NW warps that share one band engine: the whole block, or a
-// named barrier when a block runs several engines side by side.
+// Barrier of the NW warps that share one band engine (the whole block; a
+// block running several engines side by side passes its own barrier).
 struct BlockSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
-struct GroupSync {
-    int id, nthreads;
-    __device__ __forceinline__ void operator()() const
+
+// Cursor over the merged hull of this lane's line, moving right: the hull
+// word that holds the last returned member stays in a register.
+struct HullCursor {
+    int seg, word;     // position of `bits`
+    uint32_t bits;     // remaining (not yet returned) members of that word
+};
+
+__device__ __forceinline__ void cursor_at(HullCursor& hc, const BandSmem& sm, int lg, int SEGW,
+                                          int lane, int x)
+{
+    // position the cursor just after member (or position) x
+    const int s = x >> lg;
+    const int off = x - (s << lg);
+    hc.seg = s;
+    hc.word = off >> 5;
+    const uint32_t w = sm.hb[((size_t)s * SEGW + hc.word) * 32 + lane];
+    const int b = off & 31;
+    hc.bits = (b == 31) ? 0u : (w & (0xFFFFFFFEu << b));
+}
+
+__device__ __forceinline__ int cursor_next(HullCursor& hc, const BandSmem& sm, int lg, int SEGW,
+                                           int lane, uint32_t nem)
+{
+    for (;;) {
+        if (hc.bits) {
+            const int t = __ffs(hc.bits) - 1;
+            hc.bits &= hc.bits - 1;
+            return (hc.seg << lg) + hc.word * 32 + t;
+        }
+        if (++hc.word >= SEGW) {
+            const uint32_t later = (hc.seg >= 31) ? 0u : (nem & (0xFFFFFFFEu << hc.seg));
+            if (!later) return -1;
+            hc.seg = __ffs(later) - 1;
+            hc.word = 0;
+        }
+        hc.bits = sm.hb[((size_t)hc.seg * SEGW + hc.word) * 32 + lane];
+    }
+}
+
+// Output of one row (this lane's): 8 columns at a time, as two 16-byte
+// stores per array when the row layout allows it.
+struct RowOut {
+    int32_t* D;
+    int32_t* F;
+    float* dist;
+    int64_t rowoff;          // row * W
+    bool valid;              // row < H
+    bool vec;                // W % 4 == 0 and all arrays 16-byte aligned
+    __device__ __forceinline__ void finish() const {}
+    __device__ __forceinline__ void store(int j0, int cnt, const int* v, const int* f) const
     {
-        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+        if (!valid) return;
+        const int64_t i = rowoff + j0;
+        if (vec && cnt == OC) {
+            if (D) {
+                reinterpret_cast<int4*>(D + i)[0] = make_int4(v[0], v[1], v[2], v[3]);
+                reinterpret_cast<int4*>(D + i)[1] = make_int4(v[4], v[5], v[6], v[7]);
+            }
+            if (F) {
+                reinterpret_cast<int4*>(F + i)[0] = make_int4(f[0], f[1], f[2], f[3]);
+                reinterpret_cast<int4*>(F + i)[1] = make_int4(f[4], f[5], f[6], f[7]);
+            }
+            if (dist) {
+                reinterpret_cast<float4*>(dist + i)[0] =
+                    make_float4(sqrt_rn_int(v[0]), sqrt_rn_int(v[1]), sqrt_rn_int(v[2]), sqrt_rn_int(v[3]));
+                reinterpret_cast<float4*>(dist + i)[1] =
+                    make_float4(sqrt_rn_int(v[4]), sqrt_rn_int(v[5]), sqrt_rn_int(v[6]), sqrt_rn_int(v[7]));
+            }
+            return;
+        }
+#pragma unroll
+        for (int t = 0; t < OC; ++t) {
+            if (t < cnt) {
+                if (D) D[i + t] = v[t];
+                if (F) F[i + t] = f[t];
+                if (dist) dist[i + t] = sqrt_rn_int(v[t]);
+            }
+        }
     }
 };
 
-template <bool TILED, class Line, class Out, class Sync = BlockSync>
+__device__ __forceinline__ bool aligned16(const void* p)
+{
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+// Row output through the tensor memory accelerator: the warp's 32 rows x 8
+// columns are staged in shared memory (1 KB per array) and written by one
+// cp.async.bulk.tensor.2d store per array, so that the 32 row segments leave
+// the SM as whole 32-byte sectors without going through the load/store unit.
+// The tensor maps (D, F, dist; a NULL map pointer = array not written) view
+// the output as [rows][W] int32 / float32 with a box of 8 x 32.
+struct TmaRowOut {
+    const CUtensorMap* mD;
+    const CUtensorMap* mF;
+    const CUtensorMap* mS;
+    int* stage;              // this warp's 3 x 32 x 8 staging words
+    int row0;                // first row of the box (the block's first line)
+    int lane;
+    __device__ __forceinline__ void issue(const CUtensorMap* m, const int* buf, int x) const
+    {
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(buf);
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                     :: "l"(m), "r"(x), "r"(row0), "r"(sa) : "memory");
+    }
+    __device__ __forceinline__ void store(int j0, int cnt, const int* v, const int* f) const
+    {
+        (void)cnt;   // columns beyond W are clipped by the tensor map
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        __syncwarp();
+        int* sD = stage;
+        int* sF = stage + 32 * OC;
+        int* sS = stage + 64 * OC;
+        if (mD) {
+            reinterpret_cast<int4*>(sD + lane * OC)[0] = make_int4(v[0], v[1], v[2], v[3]);
+            reinterpret_cast<int4*>(sD + lane * OC)[1] = make_int4(v[4], v[5], v[6], v[7]);
+        }
+        if (mF) {
+            reinterpret_cast<int4*>(sF + lane * OC)[0] = make_int4(f[0], f[1], f[2], f[3]);
+            reinterpret_cast<int4*>(sF + lane * OC)[1] = make_int4(f[4], f[5], f[6], f[7]);
+        }
+        if (mS) {
+            reinterpret_cast<float4*>(sS + lane * OC)[0] =
+                make_float4(sqrt_rn_int(v[0]), sqrt_rn_int(v[1]), sqrt_rn_int(v[2]), sqrt_rn_int(v[3]));
+            reinterpret_cast<float4*>(sS + lane * OC)[1] =
+                make_float4(sqrt_rn_int(v[4]), sqrt_rn_int(v[5]), sqrt_rn_int(v[6]), sqrt_rn_int(v[7]));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+            if (mD) issue(mD, sD, j0);
+            if (mF) issue(mF, sF, j0);
+            if (mS) issue(mS, sS, j0);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+    }
+    __device__ __forceinline__ void finish() const
+    {
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
+    }
+};
+
+// The whole per-block computation, called by every thread of the block
+// (blockDim.x = 32 * NW, or the NW warps of one group).  Line (per lane) must
+// provide
+//   bool eval(int k, int& f) const       f(k) of this lane's line, false = infinite
+//   bool eval2(int k, int& f, int& g) const   f(k) and the feature of position k
+//   int  c(int k) const                  f(k) + k*k for a finite position
+//   bool is_zero(int k) const            f(k) == 0: position k is a source itself
+//   int  self_feature(int k) const       feature of a source position k
+// and Out must provide store(int j0, int cnt, const int* v, const int* f),
+// called by every lane of the warp at the same time with the values of its
+// line at positions j0 .. j0+cnt-1 (cnt <= OC, j0 a multiple of OC), and
+// finish(), called once by every lane at the end.  v = INT32_MAX, f = -1 where
+// the line has no finite value.
+template <class Line, class Out, class Sync = BlockSync>
 __device__ void band_envelope(const Line& line, const Out& out, const BandSmem& sm, int n,
-                              int lg, int NW, int warp = -1, Sync sync = Sync())
+                              int lg, int NW, const unsigned char* full = nullptr, int warp = -1,
+                              Sync sync = Sync())
 {
     if (warp < 0) warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -294,27 +432,94 @@ __device__ void band_envelope(const Line& line, const Out& out, const BandSmem& 
     uint32_t* hbw = sm.hb + (size_t)warp * SEGW * 32 + lane;
     for (int w = 0; w < SEGW; ++w) hbw[w * 32] = 0u;
 
-    // (1) hull of this segment of this lane's line
-    int top = -1, sec = -1, ctop = 0, csec = 0, first = -1;
-    for (int k = s0; k < s1; ++k) {
-        int fk;
-        if (!line.eval(k, fk)) continue;
-        const int ck = fk + k * k;
-        while (sec >= 0 && hidden(sec, csec, top, ctop, k, ck)) {
-            const int off = top - s0;
-            hbw[(off >> 5) * 32] &= ~(1u << (off & 31));
-            top = sec;
-            ctop = csec;
-            sec = seg_prev(sm.hb, warp, lg, SEGW, lane, top);
-            if (sec >= 0) csec = line.c(sec);
+    // (1) hull of this segment of this lane's line.  A position lying on or
+    // above the chord of its two neighbours (2 f(k) >= f(k-1) + f(k+1) + 2) is
+    // no vertex of the line's hull and is skipped; the others go through the
+    // stack algorithm, whose top three entries are kept in registers, as is
+    // the hull word of the current position (cw, word index cwi).  Where all
+    // 32 lines are sources at all 32 positions of a word (full[] set), every
+    // position is a hull vertex owning itself (a source cannot be hidden), so
+    // after the first one the word is filled at once.
+    int top = -1, sec = -1, thr = -1, ctop = 0, csec = 0, cthr = 0;
+    bool thr_known = true;
+    int fprev = 0, fcur = 0, fnext = 0;
+    bool iprev = (s0 > 0 && s0 - 1 < n) ? line.eval(s0 - 1, fprev) : false;
+    bool icur = (s0 < s1) ? line.eval(s0, fcur) : false;
+    uint32_t cw = 0u;
+    int cwi = 0;
+    // one hull word (32 positions) per outer step
+    for (int c = s0; c < s1; c += 32) {
+        cwi = (c - s0) >> 5;
+        cw = 0u;
+        const int ce = min(c + 32, s1);
+        const bool bulk = full && ce == c + 32 && full[c >> 5];
+        for (int k = c; k < ce; ++k) {
+            const bool inext = (k + 1 < n) ? line.eval(k + 1, fnext) : false;
+            const bool keep = icur && !(iprev && inext && 2 * fcur >= fprev + fnext + 2);
+            if (keep) {
+                const int ck = fcur + k * k;
+                while (sec >= 0 && hidden(sec, csec, top, ctop, k, ck)) {
+                    const int off = top - s0;
+                    if ((off >> 5) == cwi) cw &= ~(1u << (off & 31));
+                    else hbw[(off >> 5) * 32] &= ~(1u << (off & 31));
+                    top = sec;
+                    ctop = csec;
+                    if (!thr_known) {
+                        thr = -1;
+                        const int so = sec - s0;
+                        uint32_t m = ((so >> 5) == cwi ? cw : hbw[(so >> 5) * 32]) & ((1u << (so & 31)) - 1u);
+                        int w = so >> 5;
+                        while (!m && --w >= 0) m = hbw[w * 32];
+                        if (m) {
+                            thr = s0 + w * 32 + 31 - __clz(m);
+                            cthr = line.c(thr);
+                        }
+                    }
+                    sec = thr;
+                    csec = cthr;
+                    thr_known = false;
+                }
+                cw |= 1u << (k & 31);
+                thr = sec;
+                cthr = csec;
+                thr_known = true;
+                sec = top;
+                csec = ctop;
+                top = k;
+                ctop = ck;
+            }
+            iprev = icur;
+            fprev = fcur;
+            icur = inext;
+            fcur = fnext;
+            if (bulk) {
+                // every line is a source at positions c .. c+31: each is a hull
+                // vertex owning itself (a source cannot be hidden)
+                if (keep) {
+                    cw = 0xFFFFFFFFu;
+                    thr = c + 29;
+                    cthr = thr * thr;
+                    sec = c + 30;
+                    csec = sec * sec;
+                    top = c + 31;
+                    ctop = top * top;
+                    thr_known = true;
+                }
+                iprev = keep;
+                fprev = 0;
+                icur = (ce < n) ? line.eval(ce, fcur) : false;
+                break;
+            }
         }
-        const int off = k - s0;
-        hbw[(off >> 5) * 32] |= 1u << (off & 31);
-        if (first < 0) first = k;
-        sec = top;
-        csec = ctop;
-        top = k;
-        ctop = ck;
+        hbw[cwi * 32] = cw;
+    }
+    int first = -1;
+    for (int w = 0; w < SEGW; ++w) {
+        const uint32_t m = (w == cwi) ? cw : hbw[w * 32];
+        if (m) {
+            first = s0 + w * 32 + __ffs(m) - 1;
+            break;
+        }
     }
     sm.lo[warp * 32 + lane] = first;
     sm.hi[warp * 32 + lane] = top;
@@ -327,82 +532,87 @@ __device__ void band_envelope(const Line& line, const Out& out, const BandSmem& 
         sync();
     }
 
-    // (3) fill
+    // (3) fill.  cur = owner of the current position with value fcur + (j -
+    // cur)^2 and feature featcur; nxt = the next hull member (fnxt, featnxt).
+    // A source position owns itself (value 0); after a run of sources the walk
+    // resumes from the last source of the run.
     uint32_t nem = 0;
     for (int w = 0; w < NW; ++w) nem |= (uint32_t)(sm.lo[w * 32 + lane] >= 0) << w;
-    int cur = -1, fcur = 0, featcur = -1, nxt = -1, fnxt = 0;
-    bool stale = false;
+    int cur = -1, fo = 0, featcur = -1, nxt = -1, fnxt = 0, featnxt = -1;
+    bool need_next = false;
+    HullCursor hc{0, 0, 0u};
     if (nem && s0 < s1) {
         const uint32_t before = nem & ((1u << warp) - 1u);
         cur = before ? sm.hi[(31 - __clz(before)) * 32 + lane] : sm.lo[(__ffs(nem) - 1) * 32 + lane];
-        line.eval(cur, fcur);
+        line.eval(cur, fo);
         for (;;) {  // walk left while strictly better at s0
             const int p = band_prev(sm, lg, SEGW, lane, nem, cur);
             if (p < 0) break;
             int fp;
             line.eval(p, fp);
             if ((long long)fp + (long long)(s0 - p) * (s0 - p) <
-                (long long)fcur + (long long)(s0 - cur) * (s0 - cur)) {
+                (long long)fo + (long long)(s0 - cur) * (s0 - cur)) {
                 cur = p;
-                fcur = fp;
+                fo = fp;
             } else {
                 break;
             }
         }
-        nxt = band_next(sm, lg, SEGW, lane, nem, cur);
-        if (nxt >= 0) line.eval(nxt, fnxt);
-        featcur = line.feature(cur);
+        line.eval2(cur, fo, featcur);
+        need_next = true;
     }
     const int nq = ((1 << lg) + OC - 1) / OC;
     for (int q = 0; q < nq; ++q) {
         int v[OC], ft[OC];
+        const int j0 = s0 + q * OC;
+        if (full && j0 + OC <= s1 && full[j0 >> 5] && cur >= 0) {
+            // every line is a source at every position of this chunk
 #pragma unroll
-        for (int t = 0; t < OC; ++t) {
-            const int j = s0 + q * OC + t;
-            v[t] = INT32_MAX;
-            ft[t] = -1;
-            if (j < s1 && cur >= 0) {
-                while (nxt >= 0 && fnxt + (j - nxt) * (j - nxt) <= fcur + (j - cur) * (j - cur)) {
-                    cur = nxt;
-                    fcur = fnxt;
-                    stale = true;
-                    nxt = band_next(sm, lg, SEGW, lane, nem, cur);
-                    if (nxt >= 0) line.eval(nxt, fnxt);
-                }
-                if (stale) {
-                    featcur = line.feature(cur);
-                    stale = false;
-                }
-                v[t] = fcur + (j - cur) * (j - cur);
-                ft[t] = featcur;
+            for (int t = 0; t < OC; ++t) {
+                v[t] = 0;
+                ft[t] = line.self_feature(j0 + t);
             }
-        }
-        if (TILED) {
-            int4* td = reinterpret_cast<int4*>(sm.tileD + (warp * 32 + lane) * OC);
-            int4* tf = reinterpret_cast<int4*>(sm.tileF + (warp * 32 + lane) * OC);
-            td[0] = make_int4(v[0], v[1], v[2], v[3]);
-            td[1] = make_int4(v[4], v[5], v[6], v[7]);
-            tf[0] = make_int4(ft[0], ft[1], ft[2], ft[3]);
-            tf[1] = make_int4(ft[4], ft[5], ft[6], ft[7]);
-            __syncwarp();
-            const int* tD = sm.tileD + warp * 32 * OC;
-            const int* tF = sm.tileF + warp * 32 * OC;
-#pragma unroll
-            for (int p = 0; p < OC; ++p) {
-                const int ln = p * (32 / OC) + lane / OC;
-                const int t = lane % OC;
-                const int j = s0 + q * OC + t;
-                if (j < s1) out.store(ln, j, tD[ln * OC + t], tF[ln * OC + t]);
-            }
-            __syncwarp();
+            cur = j0 + OC - 1;
+            fo = 0;
+            featcur = ft[OC - 1];
+            need_next = true;
         } else {
 #pragma unroll
             for (int t = 0; t < OC; ++t) {
-                const int j = s0 + q * OC + t;
-                if (j < s1) out.store(lane, j, v[t], ft[t]);
+                const int j = j0 + t;
+                v[t] = INT32_MAX;
+                ft[t] = -1;
+                if (j < s1 && cur >= 0) {
+                    if (line.is_zero(j)) {
+                        cur = j;
+                        fo = 0;
+                        featcur = line.self_feature(j);
+                        need_next = true;
+                        v[t] = 0;
+                        ft[t] = featcur;
+                        continue;
+                    }
+                    if (need_next) {
+                        cursor_at(hc, sm, lg, SEGW, lane, cur);
+                        nxt = cursor_next(hc, sm, lg, SEGW, lane, nem);
+                        if (nxt >= 0) line.eval2(nxt, fnxt, featnxt);
+                        need_next = false;
+                    }
+                    while (nxt >= 0 && fnxt + (j - nxt) * (j - nxt) <= fo + (j - cur) * (j - cur)) {
+                        cur = nxt;
+                        fo = fnxt;
+                        featcur = featnxt;
+                        nxt = cursor_next(hc, sm, lg, SEGW, lane, nem);
+                        if (nxt >= 0) line.eval2(nxt, fnxt, featnxt);
+                    }
+                    v[t] = fo + (j - cur) * (j - cur);
+                    ft[t] = featcur;
+                }
             }
         }
+        out.store(s0 + q * OC, min(OC, s1 - (s0 + q * OC)), v, ft);
     }
+    out.finish();
 }
 
 }  // namespace edt

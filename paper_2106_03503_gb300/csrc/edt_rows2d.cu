@@ -14,6 +14,8 @@
 #include "edt_engine.cuh"
 #include "edt_internal.h"
 
+#include <cstring>
+
 namespace edt {
 
 // Encoded nearest source rows outside the band: up as int16 (-32768 = none),
@@ -29,6 +31,7 @@ struct BandRow2D {
     int i;                  // this lane's row
     int W;
     uint32_t mle, mge;      // bits at / above and at / below this row
+    uint32_t rbit;          // this row's bit
     bool valid;
 
     __device__ __forceinline__ bool parts(int k, int& up, int& dn) const
@@ -56,63 +59,123 @@ struct BandRow2D {
         const int d = min(i - up, dn - i);
         return d * d + k * k;
     }
-    __device__ __forceinline__ int feature(int k) const
+    __device__ __forceinline__ bool eval2(int k, int& f, int& g) const
     {
         int up, dn;
-        parts(k, up, dn);
-        return ((i - up <= dn - i) ? up : dn) * W + k;
+        if (!parts(k, up, dn)) return false;
+        const int du = i - up, dd = dn - i;
+        const int d = min(du, dd);
+        if (d >= 32768) return false;
+        f = d * d;
+        g = ((du <= dd) ? up : dn) * W + k;
+        return true;
     }
+    __device__ __forceinline__ bool is_zero(int k) const { return (bits[k] & rbit) != 0u; }
+    __device__ __forceinline__ int self_feature(int k) const { return i * W + k; }
 };
 
-struct BandOut2D {
-    int32_t* D;
-    int32_t* F;
-    float* dist;
-    int base, H, W;
-    __device__ __forceinline__ void store(int ln, int j, int v, int f) const
-    {
-        const int row = base + ln;
-        if (row >= H) return;
-        const int64_t idx = (int64_t)row * W + j;
-        if (D) D[idx] = v;
-        if (F) F[idx] = f;
-        if (dist) dist[idx] = sqrt_rn_int(v);
-    }
-};
-
-// Shared memory of one band block: column data + band engine.
+// Shared memory of one band block: column data (8 B per column), one flag per
+// 32 columns (all 32 rows are sources there), then the band engine.
+__host__ __device__ inline size_t band2d_col_bytes(int W)
+{
+    return (((size_t)8 * W + (size_t)(W + 31) / 32 + 15) & ~size_t(15));
+}
 static size_t band2d_smem(int W, int lg, int NW)
 {
-    return (((size_t)8 * W + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5, true);
+    return band2d_col_bytes(W) + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
-__global__ void __launch_bounds__(1024)
-k_rows2d(int H, int W, ColScratch s, int lg, int NW, int32_t* D, int32_t* F, float* dist)
+// Stage the band's column data: source word, encoded nearest source rows
+// above / below, and the per-32-column "all rows are sources" flags.  Called
+// by `nthreads` threads (a multiple of 32) with index tid.
+__device__ __forceinline__ void stage_band(const ColScratch& s, int b, int H, int W, uint32_t* sbits,
+                                           uint32_t* supdn, unsigned char* sfull, int tid, int nthreads)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* sbits = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* supdn = sbits + W;
-    const BandSmem sm = carve_band_smem(smem + (((size_t)8 * W + 15) & ~size_t(15)), NW,
-                                        (1 << lg) >> 5, true);
-    const int b = blockIdx.x;
-    const int G = b >> 5;
     const uint32_t* Cb = s.C + (int64_t)b * W;
     const uint32_t* Ub = s.U + (int64_t)b * W;
-    const uint32_t* GABg = s.GAB + (int64_t)G * W;
-    for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        const uint32_t u = Ub[j];
-        uint32_t up = u & 0xFFFFu, dn = u >> 16;
-        if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
-            const uint32_t gab = GABg[j];
-            if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
-            if (dn == (uint32_t)NONE16) dn = gab >> 16;
+    const uint32_t* GABg = s.GAB + (int64_t)(b >> 5) * W;
+    const int rows = min(32, H - b * 32);
+    const uint32_t invalid = rows >= 32 ? 0u : (FULL << rows);
+    const int Wr = (W + 31) & ~31;
+    for (int j = tid; j < Wr; j += nthreads) {
+        uint32_t w = 0u;
+        if (j < W) {
+            w = Cb[j];
+            const uint32_t u = Ub[j];
+            uint32_t up = u & 0xFFFFu, dn = u >> 16;
+            if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
+                const uint32_t gab = GABg[j];
+                if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
+                if (dn == (uint32_t)NONE16) dn = gab >> 16;
+            }
+            sbits[j] = w;
+            supdn[j] = (up == (uint32_t)NONE16 ? UP_NONE : up) | ((dn == (uint32_t)NONE16 ? DN_NONE : dn) << 16);
+            w |= invalid;
         }
-        sbits[j] = Cb[j];
-        supdn[j] = (up == (uint32_t)NONE16 ? UP_NONE : up) | ((dn == (uint32_t)NONE16 ? DN_NONE : dn) << 16);
+        const uint32_t all = __reduce_and_sync(FULL, w);
+        if ((j & 31) == 0) sfull[j >> 5] = (all == FULL) ? 1 : 0;
     }
+}
+
+// Tensor maps for TMA row stores: the output viewed as [rows][W] with an
+// 8 x 32 box (8 columns, 32 rows).  Needs W % 4 == 0 (16-byte row pitch) and a
+// 16-byte aligned base.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool make_row_map(CUtensorMap* m, void* base, bool is_float, int64_t rows, int W)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || !base || W % 4 != 0 || W < OC || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)W * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)OC, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, is_float ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2, base,
+               dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Staging per warp for TMA stores: 3 arrays x 32 rows x 8 columns.
+constexpr size_t TMA_STAGE_BYTES = 3 * 32 * OC * 4;
+
+template <bool TMA>
+__global__ void __launch_bounds__(512, 2)
+k_rows2d(int H, int W, ColScratch s, int lg, int NW, int32_t* D, int32_t* F, float* dist,
+         const __grid_constant__ CUtensorMap mD, const __grid_constant__ CUtensorMap mF,
+         const __grid_constant__ CUtensorMap mS)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint32_t* sbits = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* supdn = sbits + W;
+    unsigned char* sfull = reinterpret_cast<unsigned char*>(supdn + W);
+    // TMA staging must start on a 128-byte boundary
+    unsigned char* stage0 = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem + band2d_col_bytes(W)) + 127) & ~uintptr_t(127));
+    const BandSmem sm = carve_band_smem(stage0 + (TMA ? NW * TMA_STAGE_BYTES : 0), NW, (1 << lg) >> 5);
+    const int b = blockIdx.x;
+    stage_band(s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     BandRow2D line;
     line.bits = sbits;
     line.updn = supdn;
@@ -121,9 +184,17 @@ k_rows2d(int H, int W, ColScratch s, int lg, int NW, int32_t* D, int32_t* F, flo
     line.W = W;
     line.mle = FULL >> (31 - lane);
     line.mge = FULL << lane;
+    line.rbit = 1u << lane;
     line.valid = line.i < H;
-    const BandOut2D out{D, F, dist, b * 32, H, W};
-    band_envelope<true>(line, out, sm, W, lg, NW);
+    if (TMA) {
+        const TmaRowOut out{D ? &mD : nullptr, F ? &mF : nullptr, dist ? &mS : nullptr,
+                            reinterpret_cast<int*>(stage0 + warp * TMA_STAGE_BYTES), b * 32, lane};
+        band_envelope(line, out, sm, W, lg, NW, sfull);
+    } else {
+        const bool vec = (W % 4 == 0) && aligned16(D) && aligned16(F) && aligned16(dist);
+        const RowOut out{D, F, dist, (int64_t)line.i * W, line.valid, vec};
+        band_envelope(line, out, sm, W, lg, NW, sfull);
+    }
 }
 
 cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
@@ -131,14 +202,28 @@ cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
                           cudaStream_t stream)
 {
     (void)sm_count;
-    int max_nw = 32, lg = 0, NW = 0;
+    CUtensorMap mD, mF, mS;
+    memset(&mD, 0, sizeof(mD));
+    memset(&mF, 0, sizeof(mF));
+    memset(&mS, 0, sizeof(mS));
+    // TMA stores need more shared memory than two 16-warp blocks per SM allow
+    // at this width; direct stores at two blocks per SM measured faster.
+    bool tma = W <= 2048;
+    if (D) tma = tma && make_row_map(&mD, D, false, H, W);
+    if (F) tma = tma && make_row_map(&mF, F, false, H, W);
+    if (dist) tma = tma && make_row_map(&mS, dist, true, H, W);
+    int max_nw = 16, lg = 0, NW = 0;
+    size_t smem = 0;
     for (; max_nw >= 1; max_nw >>= 1) {
         lg = band_seg_log2(W, max_nw);
         NW = (W + (1 << lg) - 1) >> lg;
-        if (band2d_smem(W, lg, NW) <= 227 * 1024) break;
+        smem = band2d_smem(W, lg, NW) + (tma ? NW * TMA_STAGE_BYTES + 128 : 0);
+        if (smem <= 227 * 1024) break;
     }
-    const size_t smem = band2d_smem(W, lg, NW);
-    k_rows2d<<<(unsigned)g.nb, NW * 32, smem, stream>>>(H, W, s, lg, NW, D, F, dist);
+    if (tma)
+        k_rows2d<true><<<(unsigned)g.nb, NW * 32, smem, stream>>>(H, W, s, lg, NW, D, F, dist, mD, mF, mS);
+    else
+        k_rows2d<false><<<(unsigned)g.nb, NW * 32, smem, stream>>>(H, W, s, lg, NW, D, F, dist, mD, mF, mS);
     return cudaGetLastError();
 }
 
@@ -155,7 +240,7 @@ void batch_row_geometry(int W, int& lg, int& NW, int& groups)
 
 __host__ __device__ static size_t batch_group_bytes(int W, int lg, int NW)
 {
-    return (((size_t)8 * W + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5, true);
+    return band2d_col_bytes(W) + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
 size_t batch_rows_smem()
@@ -209,24 +294,10 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
             unsigned char* base = smem + (size_t)grp * batch_group_bytes(W, lg, NW);
             uint32_t* sbits = reinterpret_cast<uint32_t*>(base);
             uint32_t* supdn = sbits + W;
-            const BandSmem sm = carve_band_smem(base + (((size_t)8 * W + 15) & ~size_t(15)), NW,
-                                                (1 << lg) >> 5, true);
+            unsigned char* sfull = reinterpret_cast<unsigned char*>(supdn + W);
+            const BandSmem sm = carve_band_smem(base + band2d_col_bytes(W), NW, (1 << lg) >> 5);
             const DynSync sync{1 + grp, NW * 32};
-            const uint32_t* Cb = J.s.C + (int64_t)b * W;
-            const uint32_t* Ub = J.s.U + (int64_t)b * W;
-            const uint32_t* GABg = J.s.GAB + (int64_t)(b >> 5) * W;
-            for (int j = wg * 32 + lane; j < W; j += NW * 32) {
-                const uint32_t u = Ub[j];
-                uint32_t up = u & 0xFFFFu, dn = u >> 16;
-                if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
-                    const uint32_t gab = GABg[j];
-                    if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
-                    if (dn == (uint32_t)NONE16) dn = gab >> 16;
-                }
-                sbits[j] = Cb[j];
-                supdn[j] = (up == (uint32_t)NONE16 ? UP_NONE : up) |
-                           ((dn == (uint32_t)NONE16 ? DN_NONE : dn) << 16);
-            }
+            stage_band(J.s, b, H, W, sbits, supdn, sfull, wg * 32 + lane, NW * 32);
             sync();
             BandRow2D line;
             line.bits = sbits;
@@ -236,9 +307,11 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
             line.W = W;
             line.mle = FULL >> (31 - lane);
             line.mge = FULL << lane;
+            line.rbit = 1u << lane;
             line.valid = line.i < H;
-            const BandOut2D out{J.D, J.F, J.dist, b * 32, H, W};
-            band_envelope<true>(line, out, sm, W, lg, NW, wg, sync);
+            const bool vec = (W % 4 == 0) && aligned16(J.D) && aligned16(J.F) && aligned16(J.dist);
+            const RowOut out{J.D, J.F, J.dist, (int64_t)line.i * W, line.valid, vec};
+            band_envelope(line, out, sm, W, lg, NW, sfull, wg, sync);
         }
         __syncthreads();
     }
@@ -268,7 +341,9 @@ int batch_rows_blocks_per_sm()
 
 cudaError_t set_2d_attributes()
 {
-    return cudaFuncSetAttribute(k_rows2d, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_rows2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_rows2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 }  // namespace edt

@@ -219,6 +219,36 @@ def measure_batch(edt, torch, dev, reps=5):
             "plain": "one edt_feature call per mask from Python (ctypes) on one stream"}
 
 
+def measure_volume(edt, torch, dev, reps=10):
+    """512^3 smoothed-noise volume (sigma 4, thresholded at 0, seed 3), to
+    object, D+F: time per transform (CUDA events; the volume is 134 MB in, 1 GB
+    out, far larger than L2) and the share of each kernel (libedt tracing)."""
+    from paper_2106_03503_gb300 import inputs
+    m = torch.from_numpy(inputs.blobs_512cube()).to(dev)
+    D = torch.empty(m.shape, dtype=torch.int32, device=dev)
+    F = torch.empty_like(D)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        edt.feature(m, 0, out=(D, F, None))
+    torch.cuda.synchronize()
+    edt.trace_enable(True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        edt.feature(m, 0, out=(D, F, None))
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    kern = {k: edt.trace_read(k)[0] / reps for k in ("k_colbits", "k_ypass3d", "k_xpass3d")}
+    edt.trace_enable(False)
+    n = m.numel()
+    return {"workload": "3D 512^3 N(0,1) noise smoothed by a Gaussian (sigma 4, periodic), "
+                        "thresholded at 0 (seed 3); to object; D+F",
+            "voxels": n, "ms_per_transform": ms, "gvox_s": n / (ms / 1e3) / 1e9,
+            "effective_gbs_9B_per_vox": 9 * n / (ms / 1e3) / 1e9, "kernel_ms": kern}
+
+
 def measure_serve(edt, torch, n_jobs=600, warm=60, load=0.8, seed=5):
     """Serving: Poisson arrivals of mixed jobs (80 % 2-D squares of side
     128..4096 with Bernoulli density log-uniform 0.001..0.1, 20 % 3-D cubes of
@@ -417,6 +447,10 @@ def run_gpu(args, rank, world, local_rank):
             extras["batch"] = measure_batch(edt, torch, dev)
         except Exception as exc:  # report, do not hide
             extras["batch"] = {"error": repr(exc)}
+        try:
+            extras["volume"] = measure_volume(edt, torch, dev)
+        except Exception as exc:
+            extras["volume"] = {"error": repr(exc)}
         try:
             extras["serve"] = measure_serve(edt, torch)
         except Exception as exc:

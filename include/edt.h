@@ -82,6 +82,18 @@ edt_status edt_feature(const uint8_t *mask, int ndim, const int *shape,
                        int mode, int32_t *D, int32_t *F, float *dist,
                        edt_stream_t stream);
 
+/* Both transforms of one mask (Sec. 1.1, Fig. 1(b) and 1(c)) from a single
+ * read of it: EDT_TO_OBJECT results (distances of background pixels to the
+ * nearest object) into D_obj / F_obj and EDT_TO_BACKGROUND results (distances
+ * of object pixels to the nearest background) into D_bg / F_bg.  Each result
+ * is bit-identical to the corresponding edt_feature call.  For 2-D images
+ * the column pass runs once for both and one row launch covers both; 3-D
+ * volumes run the two transforms one after the other.  F_obj and F_bg are
+ * required, D_obj and D_bg may be NULL.  Device pointers. */
+edt_status edt_feature_pair(const uint8_t *mask, int ndim, const int *shape,
+                            int32_t *D_obj, int32_t *F_obj, int32_t *D_bg,
+                            int32_t *F_bg, edt_stream_t stream);
+
 /* The same as edt_feature with HOST buffers: mask, D, F, dist are host
  * pointers (pinned memory gives the fastest copies; pageable works).  The
  * call copies the mask to the device, runs the transform, copies the

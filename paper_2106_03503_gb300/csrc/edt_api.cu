@@ -239,6 +239,46 @@ edt_status edt_feature(const uint8_t* mask, int ndim, const int* shape, int mode
     return plain_call(mask, ndim, shape, mode, D, F, dist, (cudaStream_t)stream);
 }
 
+edt_status edt_feature_pair(const uint8_t* mask, int ndim, const int* shape, int32_t* D_obj,
+                            int32_t* F_obj, int32_t* D_bg, int32_t* F_bg, edt_stream_t stream_)
+{
+    cudaStream_t stream = (cudaStream_t)stream_;
+    edt_status st = check_shape(ndim, shape, EDT_TO_OBJECT);
+    if (st != EDT_OK) return st;
+    if (!mask || !F_obj || !F_bg) return fail(EDT_ERR_INVALID, "mask, F_obj and F_bg must not be NULL");
+    if (ndim == 3) {
+        st = plain_call(mask, 3, shape, EDT_TO_OBJECT, D_obj, F_obj, nullptr, stream);
+        if (st != EDT_OK) return st;
+        return plain_call(mask, 3, shape, EDT_TO_BACKGROUND, D_bg, F_bg, nullptr, stream);
+    }
+    int sms = 0;
+    if ((st = device_setup(&sms)) != EDT_OK) return st;
+    const int H = shape[0], W = shape[1];
+    const ColGeom g = col_geom(H, W);
+    const size_t one = col_scratch_bytes(g);
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&scratch, 2 * one, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (scratch)");
+    const ColScratch s0 = col_scratch_carve(scratch, g);
+    const ColScratch s1 = col_scratch_carve(scratch + one, g);
+    st = EDT_OK;
+    if ((e = cudaMemsetAsync(s0.cnt, 0, (size_t)g.ntiles * 4, stream)) != cudaSuccess)
+        st = cuda_fail(e, "cudaMemsetAsync");
+    if (st == EDT_OK &&
+        (e = traced("k_colbits", stream, [&] { return launch_colbits_pair(mask, g, s0, s1, stream); })) !=
+            cudaSuccess)
+        st = cuda_fail(e, "column pass launch");
+    if (st == EDT_OK &&
+        (e = traced("k_rows2d", stream, [&] {
+             return launch_rows2d_pair(H, W, g, s0, s1, D_obj, F_obj, D_bg, F_bg, stream);
+         })) != cudaSuccess)
+        st = cuda_fail(e, "row pass launch");
+    e = cudaFreeAsync(scratch, stream);
+    if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync");
+    if (st == EDT_OK) clear_error();
+    return st;
+}
+
 edt_status edt_feature_host(const uint8_t* mask, int ndim, const int* shape,
                             int mode, int32_t* D, int32_t* F, float* dist,
                             edt_stream_t stream_)

@@ -94,11 +94,73 @@ __device__ __forceinline__ uint32_t load_row_bits(const uint8_t* __restrict__ p,
     return bits;
 }
 
+// Rows of band `band` that lie inside the image, as a bit mask.
+__device__ __forceinline__ uint32_t band_rows_mask(const ColGeom& g, int band)
+{
+    const int rows = g.rows - band * 32;
+    return rows >= 32 ? FULL : ((1u << rows) - 1u);
+}
+
+// Step (2) for one column: nearest source above / below each band of group G
+// inside the group, and the group's first / last source row.  `invert` takes
+// the complement of the words (the other class as sources) within the image.
+__device__ __forceinline__ void group_scan(const ColGeom& g, const ColScratch& s, uint32_t (*cw)[32],
+                                           uint32_t (*upS)[32], bool invert, int G, int64_t col)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t W = g.cols;
+    const int b0 = G * 32;
+    const int nbg = min(32, g.nb - b0);
+    int last = NONE16, first = NONE16;
+    for (int bl = 0; bl < nbg; ++bl) {
+        uint32_t w = cw[bl][lane];
+        if (invert) w = ~w & band_rows_mask(g, b0 + bl);
+        upS[bl][lane] = (uint32_t)last;
+        if (w) {
+            last = (b0 + bl) * 32 + 31 - __clz(w);
+            if (first == NONE16) first = (b0 + bl) * 32 + __ffs(w) - 1;
+        }
+    }
+    int nxt = NONE16;
+    for (int bl = nbg - 1; bl >= 0; --bl) {
+        uint32_t w = cw[bl][lane];
+        if (invert) w = ~w & band_rows_mask(g, b0 + bl);
+        s.U[(int64_t)(b0 + bl) * W + col] = upS[bl][lane] | ((uint32_t)nxt << 16);
+        if (w) nxt = (b0 + bl) * 32 + __ffs(w) - 1;
+    }
+    s.GFL[(int64_t)G * W + col] = (uint32_t)first | ((uint32_t)last << 16);
+}
+
+// Step (3) for one column: nearest source above / below every group, over the
+// whole column, from the groups' first / last rows.  tmp: 32 words of scratch.
+__device__ __forceinline__ void link_groups(const ColGeom& g, const ColScratch& s, uint32_t (*tmp)[32],
+                                            int64_t col)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t W = g.cols;
+    int above = NONE16;
+    for (int G2 = 0; G2 < g.nG; ++G2) {
+        const uint32_t v = __ldcg(s.GFL + (int64_t)G2 * W + col);
+        tmp[G2][lane] = (uint32_t)above;
+        if ((v >> 16) != (uint32_t)NONE16) above = (int)(v >> 16);
+    }
+    int below = NONE16;
+    for (int G2 = g.nG - 1; G2 >= 0; --G2) {
+        const uint32_t v = __ldcg(s.GFL + (int64_t)G2 * W + col);
+        s.GAB[(int64_t)G2 * W + col] = tmp[G2][lane] | ((uint32_t)below << 16);
+        if ((v & 0xFFFFu) != (uint32_t)NONE16) below = (int)(v & 0xFFFFu);
+    }
+}
+
 // The work of one warp: columns [32*tile, 32*tile + 32) x bands of group G.
-// cw and upS are this warp's 32 x 32 shared scratch tiles.
-template <bool VEC>
+// cw and upS are this warp's 32 x 32 shared scratch tiles.  With PAIR the
+// warp serves both transforms from one read of the mask: s gets the summaries
+// with the nonzero bytes as sources, s1 those with the zero bytes (the column
+// words of the second are the complement of s.C inside the image and are not
+// stored).
+template <bool VEC, bool PAIR>
 __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g, int mode,
-                             const ColScratch& s, int64_t tile, int G,
+                             const ColScratch& s, const ColScratch& s1, int64_t tile, int G,
                              uint32_t (*cw)[32], uint32_t (*upS)[32])
 {
     const int lane = threadIdx.x & 31;
@@ -109,6 +171,7 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
     const int nbg = min(32, g.nb - b0);
     const int ncols = (W - col0) < 32 ? (int)(W - col0) : 32;
     const uint32_t colvalid = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
+    const bool invert_in = !PAIR && mode == EDT_TO_BACKGROUND;
 
     // (1) source bits of 32 rows x 32 columns per band, transposed by ballots
     for (int bl = 0; bl < nbg; bl += 4) {
@@ -119,7 +182,7 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
             src[u] = 0;
             if (bl + u < nbg && row < g.rows) {
                 src[u] = load_row_bits<VEC>(mask + (int64_t)row * W + col0, ncols);
-                if (mode == EDT_TO_BACKGROUND) src[u] = ~src[u];
+                if (invert_in) src[u] = ~src[u];
                 src[u] &= colvalid;
             }
         }
@@ -140,22 +203,8 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
 
     // (2) nearest source above / below each band inside the group
     if (col < W) {
-        int last = NONE16, first = NONE16;
-        for (int bl = 0; bl < nbg; ++bl) {
-            const uint32_t w = cw[bl][lane];
-            upS[bl][lane] = (uint32_t)last;
-            if (w) {
-                last = (b0 + bl) * 32 + 31 - __clz(w);
-                if (first == NONE16) first = (b0 + bl) * 32 + __ffs(w) - 1;
-            }
-        }
-        int nxt = NONE16;
-        for (int bl = nbg - 1; bl >= 0; --bl) {
-            const uint32_t w = cw[bl][lane];
-            s.U[(int64_t)(b0 + bl) * W + col] = upS[bl][lane] | ((uint32_t)nxt << 16);
-            if (w) nxt = (b0 + bl) * 32 + __ffs(w) - 1;
-        }
-        s.GFL[(int64_t)G * W + col] = (uint32_t)first | ((uint32_t)last << 16);
+        group_scan(g, s, cw, upS, false, G, col);
+        if (PAIR) group_scan(g, s1, cw, upS, true, G, col);
     }
 
     // (3) the last group of this tile to finish links the groups
@@ -167,33 +216,23 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
     if (old != (unsigned)(g.nG - 1)) return;
     __threadfence();
     if (col < W) {
-        int above = NONE16;
-        for (int G2 = 0; G2 < g.nG; ++G2) {
-            const uint32_t v = __ldcg(s.GFL + (int64_t)G2 * W + col);
-            cw[G2][lane] = (uint32_t)above;
-            if ((v >> 16) != (uint32_t)NONE16) above = (int)(v >> 16);
-        }
-        int below = NONE16;
-        for (int G2 = g.nG - 1; G2 >= 0; --G2) {
-            const uint32_t v = __ldcg(s.GFL + (int64_t)G2 * W + col);
-            s.GAB[(int64_t)G2 * W + col] = cw[G2][lane] | ((uint32_t)below << 16);
-            if ((v & 0xFFFFu) != (uint32_t)NONE16) below = (int)(v & 0xFFFFu);
-        }
+        link_groups(g, s, cw, col);
+        if (PAIR) link_groups(g, s1, cw, col);
     }
     __syncwarp();
     if (lane == 0) s.cnt[tile] = 0u;  // ready for the next call
 }
 
-template <bool VEC>
+template <bool VEC, bool PAIR>
 __global__ void __launch_bounds__(K1_WARPS * 32)
-k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s)
+k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s, ColScratch s1)
 {
     __shared__ uint32_t cw[K1_WARPS][32][32];   // [warp][band][column]
     __shared__ uint32_t upS[K1_WARPS][32][32];  // forward-scan results
     const int warp = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp;
     if (gw >= g.ntiles * (int64_t)g.nG) return;  // whole warp; no block sync below
-    colbits_warp<VEC>(mask, g, mode, s, gw % g.ntiles, (int)(gw / g.ntiles), cw[warp], upS[warp]);
+    colbits_warp<VEC, PAIR>(mask, g, mode, s, s1, gw % g.ntiles, (int)(gw / g.ntiles), cw[warp], upS[warp]);
 }
 
 // Persistent column pass over every job of a batch: warp units are numbered
@@ -218,9 +257,11 @@ k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
         const ColScratch s = J.s;
         const int64_t local = gw - J.k1_first;
         if (J.vec)
-            colbits_warp<true>(J.mask, g, J.mode, s, local % g.ntiles, (int)(local / g.ntiles), cw[warp], upS[warp]);
+            colbits_warp<true, false>(J.mask, g, J.mode, s, s, local % g.ntiles, (int)(local / g.ntiles),
+                                      cw[warp], upS[warp]);
         else
-            colbits_warp<false>(J.mask, g, J.mode, s, local % g.ntiles, (int)(local / g.ntiles), cw[warp], upS[warp]);
+            colbits_warp<false, false>(J.mask, g, J.mode, s, s, local % g.ntiles, (int)(local / g.ntiles),
+                                       cw[warp], upS[warp]);
         __syncwarp();
     }
 }
@@ -248,9 +289,24 @@ cudaError_t launch_colbits(const uint8_t* mask, const ColGeom& g, int mode,
     const int64_t blocks = (warps + K1_WARPS - 1) / K1_WARPS;
     const bool vec = (g.cols % 16 == 0) && ((reinterpret_cast<uintptr_t>(mask) & 15) == 0);
     if (vec)
-        k_colbits<true><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s);
+        k_colbits<true, false><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s, s);
     else
-        k_colbits<false><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s);
+        k_colbits<false, false><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s, s);
+    return cudaGetLastError();
+}
+
+// Both transforms' summaries from one read of the mask (s: nonzero bytes are
+// the sources, s1: zero bytes; s1.C is not written).
+cudaError_t launch_colbits_pair(const uint8_t* mask, const ColGeom& g, const ColScratch& s,
+                                const ColScratch& s1, cudaStream_t stream)
+{
+    const int64_t warps = g.ntiles * (int64_t)g.nG;
+    const int64_t blocks = (warps + K1_WARPS - 1) / K1_WARPS;
+    const bool vec = (g.cols % 16 == 0) && ((reinterpret_cast<uintptr_t>(mask) & 15) == 0);
+    if (vec)
+        k_colbits<true, true><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, 0, s, s1);
+    else
+        k_colbits<false, true><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, 0, s, s1);
     return cudaGetLastError();
 }
 

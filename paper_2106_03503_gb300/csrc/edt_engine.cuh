@@ -370,12 +370,11 @@ struct TmaRowOut {
     }
     __device__ __forceinline__ void store(int j0, int cnt, const int* v, const int* f) const
     {
-        (void)cnt;   // columns beyond W are clipped by the tensor map
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         __syncwarp();
-        int* sD = stage;
-        int* sF = stage + 32 * OC;
-        int* sS = stage + 64 * OC;
+        int* sD = stage;                       // arrays present, back to back
+        int* sF = sD + (mD ? 32 * OC : 0);
+        int* sS = sF + (mF ? 32 * OC : 0);
         if (mD) {
             reinterpret_cast<int4*>(sD + lane * OC)[0] = make_int4(v[0], v[1], v[2], v[3]);
             reinterpret_cast<int4*>(sD + lane * OC)[1] = make_int4(v[4], v[5], v[6], v[7]);
@@ -392,7 +391,7 @@ struct TmaRowOut {
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) {
+        if (lane == 0 && cnt > 0) {   // never a box that starts past the row end
             if (mD) issue(mD, sD, j0);
             if (mF) issue(mF, sF, j0);
             if (mS) issue(mS, sS, j0);

@@ -45,6 +45,11 @@ cudaError_t launch_colbits(const uint8_t* mask, const ColGeom& g, int mode,
 cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
                           int32_t* D, int32_t* F, float* dist, int sm_count,
                           cudaStream_t stream);
+cudaError_t launch_colbits_pair(const uint8_t* mask, const ColGeom& g, const ColScratch& s,
+                                const ColScratch& s1, cudaStream_t stream);
+cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch& s_obj,
+                               const ColScratch& s_bg, int32_t* D_obj, int32_t* F_obj,
+                               int32_t* D_bg, int32_t* F_bg, cudaStream_t stream);
 cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
                            const ColScratch& s, uint32_t* P, cudaStream_t stream);
 cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,

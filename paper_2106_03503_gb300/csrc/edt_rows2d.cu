@@ -26,7 +26,7 @@ constexpr uint32_t DN_NONE = 0xFFFFu;
 
 struct BandRow2D {
     const uint32_t* bits;   // [W]: source bits of the band's 32 rows
-    const uint32_t* updn;   // [W]: encoded up | dn << 16
+    const uint32_t* updn;   // [W]: encoded up | dn << 16 (shared or global memory)
     int base;               // first row of the band
     int i;                  // this lane's row
     int W;
@@ -89,7 +89,8 @@ static size_t band2d_smem(int W, int lg, int NW)
 // above / below, and the per-32-column "all rows are sources" flags.  Called
 // by `nthreads` threads (a multiple of 32) with index tid.
 __device__ __forceinline__ void stage_band(const ColScratch& s, int b, int H, int W, uint32_t* sbits,
-                                           uint32_t* supdn, unsigned char* sfull, int tid, int nthreads)
+                                           uint32_t* supdn, unsigned char* sfull, int tid, int nthreads,
+                                           bool invert = false)
 {
     const uint32_t* Cb = s.C + (int64_t)b * W;
     const uint32_t* Ub = s.U + (int64_t)b * W;
@@ -101,6 +102,7 @@ __device__ __forceinline__ void stage_band(const ColScratch& s, int b, int H, in
         uint32_t w = 0u;
         if (j < W) {
             w = Cb[j];
+            if (invert) w = ~w & ~invalid;   // the other class, rows inside the image
             const uint32_t u = Ub[j];
             uint32_t up = u & 0xFFFFu, dn = u >> 16;
             if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
@@ -156,11 +158,24 @@ bool make_row_map(CUtensorMap* m, void* base, bool is_float, int64_t rows, int W
 // Staging per warp for TMA stores: 3 arrays x 32 rows x 8 columns.
 constexpr size_t TMA_STAGE_BYTES = 3 * 32 * OC * 4;
 
+// One transform of the row kernel: its column-pass scratch, whether its
+// sources are the complement of the stored column words, and its outputs.
+struct RowJob {
+    ColScratch s;
+    int invert;
+    int32_t* D;
+    int32_t* F;
+    float* dist;
+};
+
+// Blocks [0, nb) run job 0, blocks [nb, 2 nb) job 1 (when two transforms of
+// one mask are fused); one block per band of 32 rows.
 template <bool TMA>
 __global__ void __launch_bounds__(512, 2)
-k_rows2d(int H, int W, ColScratch s, int lg, int NW, int32_t* D, int32_t* F, float* dist,
-         const __grid_constant__ CUtensorMap mD, const __grid_constant__ CUtensorMap mF,
-         const __grid_constant__ CUtensorMap mS)
+k_rows2d(int H, int W, int nb, RowJob J0, RowJob J1, int lg, int NW,
+         const __grid_constant__ CUtensorMap mD0, const __grid_constant__ CUtensorMap mF0,
+         const __grid_constant__ CUtensorMap mS0, const __grid_constant__ CUtensorMap mD1,
+         const __grid_constant__ CUtensorMap mF1, const __grid_constant__ CUtensorMap mS1)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     uint32_t* sbits = reinterpret_cast<uint32_t*>(smem);
@@ -170,8 +185,10 @@ k_rows2d(int H, int W, ColScratch s, int lg, int NW, int32_t* D, int32_t* F, flo
     unsigned char* stage0 = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem + band2d_col_bytes(W)) + 127) & ~uintptr_t(127));
     const BandSmem sm = carve_band_smem(stage0 + (TMA ? NW * TMA_STAGE_BYTES : 0), NW, (1 << lg) >> 5);
-    const int b = blockIdx.x;
-    stage_band(s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x);
+    const bool second = (int)blockIdx.x >= nb;
+    const RowJob& J = second ? J1 : J0;
+    const int b = second ? (int)blockIdx.x - nb : (int)blockIdx.x;
+    stage_band(J.s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x, J.invert != 0);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -187,31 +204,33 @@ k_rows2d(int H, int W, ColScratch s, int lg, int NW, int32_t* D, int32_t* F, flo
     line.rbit = 1u << lane;
     line.valid = line.i < H;
     if (TMA) {
-        const TmaRowOut out{D ? &mD : nullptr, F ? &mF : nullptr, dist ? &mS : nullptr,
+        const TmaRowOut out{J.D ? (second ? &mD1 : &mD0) : nullptr, J.F ? (second ? &mF1 : &mF0) : nullptr,
+                            J.dist ? (second ? &mS1 : &mS0) : nullptr,
                             reinterpret_cast<int*>(stage0 + warp * TMA_STAGE_BYTES), b * 32, lane};
         band_envelope(line, out, sm, W, lg, NW, sfull);
     } else {
-        const bool vec = (W % 4 == 0) && aligned16(D) && aligned16(F) && aligned16(dist);
-        const RowOut out{D, F, dist, (int64_t)line.i * W, line.valid, vec};
+        const bool vec = (W % 4 == 0) && aligned16(J.D) && aligned16(J.F) && aligned16(J.dist);
+        const RowOut out{J.D, J.F, J.dist, (int64_t)line.i * W, line.valid, vec};
         band_envelope(line, out, sm, W, lg, NW, sfull);
     }
 }
 
-cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
-                          int32_t* D, int32_t* F, float* dist, int sm_count,
-                          cudaStream_t stream)
+// Row pass for one transform (J1 unused) or two transforms of one mask.
+static cudaError_t launch_rows(int H, int W, const ColGeom& g, const RowJob& J0, const RowJob* J1,
+                               cudaStream_t stream)
 {
-    (void)sm_count;
-    CUtensorMap mD, mF, mS;
-    memset(&mD, 0, sizeof(mD));
-    memset(&mF, 0, sizeof(mF));
-    memset(&mS, 0, sizeof(mS));
-    // TMA stores need more shared memory than two 16-warp blocks per SM allow
-    // at this width; direct stores at two blocks per SM measured faster.
+    CUtensorMap m[6];
+    memset(m, 0, sizeof(m));
+    const RowJob* jobs[2] = {&J0, J1};
+    // TMA stores where the shared memory still allows two blocks per SM
+    // (widths up to 2048); per-lane 16-byte stores otherwise
     bool tma = W <= 2048;
-    if (D) tma = tma && make_row_map(&mD, D, false, H, W);
-    if (F) tma = tma && make_row_map(&mF, F, false, H, W);
-    if (dist) tma = tma && make_row_map(&mS, dist, true, H, W);
+    for (int k = 0; k < 2 && tma; ++k) {
+        if (!jobs[k]) continue;
+        if (jobs[k]->D) tma = tma && make_row_map(&m[3 * k + 0], jobs[k]->D, false, H, W);
+        if (jobs[k]->F) tma = tma && make_row_map(&m[3 * k + 1], jobs[k]->F, false, H, W);
+        if (jobs[k]->dist) tma = tma && make_row_map(&m[3 * k + 2], jobs[k]->dist, true, H, W);
+    }
     int max_nw = 16, lg = 0, NW = 0;
     size_t smem = 0;
     for (; max_nw >= 1; max_nw >>= 1) {
@@ -220,11 +239,35 @@ cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
         smem = band2d_smem(W, lg, NW) + (tma ? NW * TMA_STAGE_BYTES + 128 : 0);
         if (smem <= 227 * 1024) break;
     }
+    const RowJob j1 = J1 ? *J1 : J0;
+    const unsigned blocks = (unsigned)(g.nb * (J1 ? 2 : 1));
     if (tma)
-        k_rows2d<true><<<(unsigned)g.nb, NW * 32, smem, stream>>>(H, W, s, lg, NW, D, F, dist, mD, mF, mS);
+        k_rows2d<true><<<blocks, NW * 32, smem, stream>>>(H, W, g.nb, J0, j1, lg, NW, m[0], m[1], m[2], m[3],
+                                                          m[4], m[5]);
     else
-        k_rows2d<false><<<(unsigned)g.nb, NW * 32, smem, stream>>>(H, W, s, lg, NW, D, F, dist, mD, mF, mS);
+        k_rows2d<false><<<blocks, NW * 32, smem, stream>>>(H, W, g.nb, J0, j1, lg, NW, m[0], m[1], m[2], m[3],
+                                                           m[4], m[5]);
     return cudaGetLastError();
+}
+
+cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
+                          int32_t* D, int32_t* F, float* dist, int sm_count,
+                          cudaStream_t stream)
+{
+    (void)sm_count;
+    const RowJob J{s, 0, D, F, dist};
+    return launch_rows(H, W, g, J, nullptr, stream);
+}
+
+cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch& s_obj,
+                               const ColScratch& s_bg, int32_t* D_obj, int32_t* F_obj,
+                               int32_t* D_bg, int32_t* F_bg, cudaStream_t stream)
+{
+    ColScratch sb = s_bg;
+    sb.C = s_obj.C;   // the to-background sources are the complement of these words
+    const RowJob J0{s_obj, 0, D_obj, F_obj, nullptr};
+    const RowJob J1{sb, 1, D_bg, F_bg, nullptr};
+    return launch_rows(H, W, g, J0, &J1, stream);
 }
 
 // --- batched row pass -------------------------------------------------------

@@ -55,6 +55,7 @@ _lib.edt_sq2d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _v
 _lib.edt_sq3d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
 _lib.edt_feature.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.edt_feature_host.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.edt_feature_pair.argtypes = [_vp, ctypes.c_int, _i32p, _vp, _vp, _vp, _vp, _vp]
 _lib.edt_trace_enable.argtypes = [ctypes.c_int]
 _lib.edt_trace_enable.restype = ctypes.c_int
 _lib.edt_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -62,10 +63,10 @@ _lib.edt_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)
 _lib.edt_trace_read.restype = ctypes.c_int
 _lib.edt_last_error.restype = ctypes.c_char_p
 _lib.edt_version.restype = ctypes.c_char_p
-for _name in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host"):
+for _name in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host", "edt_feature_pair"):
     getattr(_lib, _name).restype = ctypes.c_int
 
-EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host", "edt_plan_create",
+EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_pair", "edt_feature_host", "edt_plan_create",
            "edt_plan_destroy", "edt_batch", "edt_serve_create", "edt_serve_submit",
            "edt_serve_poll", "edt_serve_destroy", "edt_trace_enable", "edt_trace_read",
            "edt_last_error", "edt_version")
@@ -282,6 +283,23 @@ def feature(mask, mode: int = TO_OBJECT, want_D: bool = True, want_dist: bool = 
     _check(_lib.edt_feature(_ptr(m), m.dim(), _shape_arr(m.shape), int(mode), _ptr(D), _ptr(F),
                             _ptr(dist), _stream_handle(stream)))
     return (D, F, dist) if (want_dist or (out is not None and out[2] is not None)) else (D, F)
+
+
+def feature_pair(mask, want_D: bool = True, out=None, stream=None):
+    """Both transforms of one mask from one read of it: returns
+    ((D_obj, F_obj), (D_bg, F_bg)) -- to object and to background."""
+    m = _mask_arg(mask)
+    if out is not None:
+        (Do, Fo), (Db, Fb) = out
+    else:
+        mk = lambda: torch.empty(m.shape, dtype=torch.int32, device=m.device)  # noqa: E731
+        Do = mk() if want_D else None
+        Fo = mk()
+        Db = mk() if want_D else None
+        Fb = mk()
+    _check(_lib.edt_feature_pair(_ptr(m), m.dim(), _shape_arr(m.shape), _ptr(Do), _ptr(Fo), _ptr(Db),
+                                 _ptr(Fb), _stream_handle(stream)))
+    return (Do, Fo), (Db, Fb)
 
 
 def feature_host(mask: np.ndarray, mode: int = TO_OBJECT, D=None, F=None, dist=None,

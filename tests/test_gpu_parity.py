@@ -111,3 +111,23 @@ def test_invalid_arguments_raise():
     with pytest.raises(edt.EdtError) as e:
         edt.feature(big)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (5, 7), (33, 64), (100, 100), (257, 1000), (1031, 97),
+                                   (70, 2048), (40, 4104), (3, 9, 17), (20, 33, 40)])
+def test_pair_equals_two_calls(shape):
+    """edt_feature_pair: both transforms from one mask read, bit-identical to
+    two edt_feature calls, and D exact against the oracle."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    for k, p in enumerate([0.0, 0.02, 0.5, 1.0]):
+        m_np = inputs.bernoulli_mask(shape, p, 77 + k)
+        m = torch.from_numpy(m_np).cuda()
+        (Do, Fo), (Db, Fb) = edt.feature_pair(m)
+        Dr0, Fr0 = edt.feature(m, 0)
+        Dr1, Fr1 = edt.feature(m, 1)
+        torch.cuda.synchronize()
+        assert torch.equal(Do, Dr0) and torch.equal(Fo, Fr0)
+        assert torch.equal(Db, Dr1) and torch.equal(Fb, Fr1)
+        np.testing.assert_array_equal(Do.cpu().numpy(), oracle.edt(m_np, 0)[0])
+        np.testing.assert_array_equal(Db.cpu().numpy(), oracle.edt(m_np, 1)[0])

@@ -188,7 +188,7 @@ k_xpass3d(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D,
     line.W = W;
     line.valid = row < nrows;
     line.self = ((uint32_t)line.z << 16) | (uint32_t)line.y;
-    const bool vec = (W % 4 == 0) && aligned16(D) && aligned16(F) && aligned16(dist);
+    const int vec = row_vec_width(W, D, F, dist);
     const RowOut out{D, F, dist, row * W, row < nrows, vec};
     band_envelope(line, out, sm, W, lg, NW, nullptr);
 }

@@ -302,21 +302,59 @@ __device__ __forceinline__ int cursor_next(HullCursor& hc, const BandSmem& sm, i
     }
 }
 
-// Output of one row (this lane's): 8 columns at a time, as two 16-byte
-// stores per array when the row layout allows it.
+__device__ __forceinline__ bool aligned16(const void* p)
+{
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+// One 32-byte store (sm_100 and later): 8 consecutive words at a 32-byte
+// aligned address, a whole sector in one instruction.
+__device__ __forceinline__ void st_v8(void* q, int a0, int a1, int a2, int a3, int a4, int a5, int a6,
+                                      int a7)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(q), "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7)
+                 : "memory");
+}
+
+// Widest vector store every row chunk of OC words of all arrays allows:
+// 2 = 32-byte stores (W % 8 == 0, arrays 32-byte aligned), 1 = 16-byte stores
+// (W % 4 == 0, 16-byte aligned), 0 = single words.  NULL arrays do not count.
+__device__ __forceinline__ int row_vec_width(int W, const void* D, const void* F, const void* dist)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(D) | reinterpret_cast<uintptr_t>(F) |
+                        reinterpret_cast<uintptr_t>(dist);
+    if (W % 8 == 0 && (a & 31) == 0) return 2;
+    if (W % 4 == 0 && (a & 15) == 0) return 1;
+    return 0;
+}
+
+// Output of one row (this lane's): 8 columns at a time, as one 32-byte or two
+// 16-byte stores per array when the row layout allows it.
 struct RowOut {
     int32_t* D;
     int32_t* F;
     float* dist;
     int64_t rowoff;          // row * W
     bool valid;              // row < H
-    bool vec;                // W % 4 == 0 and all arrays 16-byte aligned
+    int vec;                 // row_vec_width of the arrays
     __device__ __forceinline__ void finish() const {}
     __device__ __forceinline__ void store(int j0, int cnt, const int* v, const int* f) const
     {
         if (!valid) return;
         const int64_t i = rowoff + j0;
-        if (vec && cnt == OC) {
+        if (vec == 2 && cnt == OC) {
+            if (D) st_v8(D + i, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]);
+            if (F) st_v8(F + i, f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7]);
+            if (dist) {
+                int r[OC];
+#pragma unroll
+                for (int t = 0; t < OC; ++t) r[t] = __float_as_int(sqrt_rn_int(v[t]));
+                st_v8(dist + i, r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7]);
+            }
+            return;
+        }
+        if (vec == 1 && cnt == OC) {
             if (D) {
                 reinterpret_cast<int4*>(D + i)[0] = make_int4(v[0], v[1], v[2], v[3]);
                 reinterpret_cast<int4*>(D + i)[1] = make_int4(v[4], v[5], v[6], v[7]);
@@ -343,11 +381,6 @@ struct RowOut {
         }
     }
 };
-
-__device__ __forceinline__ bool aligned16(const void* p)
-{
-    return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
-}
 
 // Row output through the tensor memory accelerator: the warp's 32 rows x 8
 // columns are staged in shared memory (1 KB per array) and written by one

@@ -209,7 +209,7 @@ k_rows2d(int H, int W, int nb, RowJob J0, RowJob J1, int lg, int NW,
                             reinterpret_cast<int*>(stage0 + warp * TMA_STAGE_BYTES), b * 32, lane};
         band_envelope(line, out, sm, W, lg, NW, sfull);
     } else {
-        const bool vec = (W % 4 == 0) && aligned16(J.D) && aligned16(J.F) && aligned16(J.dist);
+        const int vec = row_vec_width(W, J.D, J.F, J.dist);
         const RowOut out{J.D, J.F, J.dist, (int64_t)line.i * W, line.valid, vec};
         band_envelope(line, out, sm, W, lg, NW, sfull);
     }
@@ -352,7 +352,7 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
             line.mge = FULL << lane;
             line.rbit = 1u << lane;
             line.valid = line.i < H;
-            const bool vec = (W % 4 == 0) && aligned16(J.D) && aligned16(J.F) && aligned16(J.dist);
+            const int vec = row_vec_width(W, J.D, J.F, J.dist);
             const RowOut out{J.D, J.F, J.dist, (int64_t)line.i * W, line.valid, vec};
             band_envelope(line, out, sm, W, lg, NW, sfull, wg, sync);
         }

@@ -7,14 +7,14 @@ import pytest
 
 import oracle
 from golden_io import grid, six_object_mask
-from gpu_check import check_against_oracle, run_gpu
+from gpu_check import check_against_oracle, feature_valid_fast, run_gpu
 from paper_2106_03503_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
 SHAPES_2D = [(1, 1), (1, 2), (2, 1), (1, 37), (37, 1), (5, 7), (31, 33), (32, 32), (33, 31),
              (64, 100), (100, 64), (129, 257), (257, 1000), (1000, 37), (97, 1031), (1031, 97),
-             (2, 4099), (3001, 5), (333, 2048), (65, 8192)]
+             (2, 4099), (3001, 5), (333, 2048), (33, 4100), (65, 8192)]
 DENS = [0.0005, 0.01, 0.1, 0.5, 0.97]
 
 
@@ -131,3 +131,27 @@ def test_pair_equals_two_calls(shape):
         assert torch.equal(Db, Dr1) and torch.equal(Fb, Fr1)
         np.testing.assert_array_equal(Do.cpu().numpy(), oracle.edt(m_np, 0)[0])
         np.testing.assert_array_equal(Db.cpu().numpy(), oracle.edt(m_np, 1)[0])
+
+
+@pytest.mark.parametrize("shape", [(40, 4104), (33, 8192), (9, 17, 1000)])
+@pytest.mark.parametrize("offset", [0, 4, 1, 2])
+def test_output_alignments(shape, offset):
+    """Outputs that start 32-byte aligned, only 16-byte aligned, or 4- and
+    8-byte aligned: each takes its own store width and all give the same
+    result."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    m_np = inputs.bernoulli_mask(shape, 0.01, 91)
+    m = torch.from_numpy(m_np).cuda()
+    n = m_np.size
+    bufs = [torch.zeros(n + 8, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.float32)]
+    D, F, dist = (b[offset:offset + n].view(shape) for b in bufs)
+    edt.feature(m, 0, out=(D, F, dist))
+    torch.cuda.synchronize()
+    Do = oracle.edt(m_np, 0)[0]
+    np.testing.assert_array_equal(D.cpu().numpy(), Do)
+    assert feature_valid_fast(m_np, 0, Do, F.cpu().numpy()) is None
+    np.testing.assert_array_equal(dist.cpu().numpy().view(np.uint32), oracle.sqrt_f32(Do).view(np.uint32))
+    for b in bufs:   # nothing written outside the views
+        h = b.cpu().numpy()
+        assert not h[:offset].any() and not h[offset + n:].any()

@@ -31,10 +31,12 @@
 //       by the classic bridge walk (drop the left top while it is hidden
 //       between its predecessor and the right bottom; drop the right bottom
 //       while it is hidden between the left top and its successor).
-//   (3) Each (segment, line) fills its positions: the owner of a position is
-//       the hull member with the smallest value there; owners move right
-//       monotonically with the position, and along the hull the values at a
-//       fixed position are unimodal, so a walk finds them.  Each lane writes
+//   (3) The warps fill the positions in units taken in turn from a shared
+//       counter (so that costly parts of the lines are spread over all
+//       warps): the owner of a position is the hull member with the smallest
+//       value there; owners move right monotonically with the position, and
+//       along the hull the values at a fixed position are unimodal, so a walk
+//       finds them.  Each lane writes
 //       its values 8 positions at a time: a row line as two 16-byte stores
 //       per array (one whole 32-byte sector), a column line as single stores
 //       that are coalesced across the 32 neighbouring lines.
@@ -117,11 +119,12 @@ struct BandSmem {
     uint32_t* hb;   // [NW][SEGW][32] hull bits: segment, word, lane
     int* lo;        // [NW][32] first hull member of (segment, line), -1 none
     int* hi;        // [NW][32] last hull member
+    int* ctr;       // next fill unit to hand out
 };
 
 __host__ __device__ inline size_t band_smem_bytes(int NW, int SEGW)
 {
-    return (size_t)NW * SEGW * 32 * 4 + (size_t)NW * 64 * 4;
+    return (size_t)NW * SEGW * 32 * 4 + (size_t)NW * 64 * 4 + 16;
 }
 
 __device__ __forceinline__ BandSmem carve_band_smem(unsigned char* base, int NW, int SEGW)
@@ -130,7 +133,16 @@ __device__ __forceinline__ BandSmem carve_band_smem(unsigned char* base, int NW,
     s.hb = reinterpret_cast<uint32_t*>(base);
     s.lo = reinterpret_cast<int*>(base + (size_t)NW * SEGW * 32 * 4);
     s.hi = s.lo + NW * 32;
+    s.ctr = s.hi + NW * 32;
     return s;
+}
+
+// Positions per fill unit: about four units per warp, a multiple of 32
+// between 32 and 256.
+__host__ __device__ inline int band_fill_unit(int n, int NW)
+{
+    int u = (n / (4 * NW) + 31) & ~31;
+    return u < 32 ? 32 : (u > 256 ? 256 : u);
 }
 
 // Segment length (power of two, >= 32) and segment count for a line of n
@@ -438,6 +450,91 @@ struct TmaRowOut {
     }
 };
 
+// Fill positions [a, b) of this lane's line from its merged hull.  cur = owner
+// of the current position with value fo + (j - cur)^2 and feature featcur;
+// nxt = the next hull member (fnxt, featnxt).  A source position owns itself
+// (value 0); after a run of sources the walk resumes from the last source of
+// the run.  Stores go out OC positions at a time (a is a multiple of OC).
+template <class Line, class Out>
+__device__ void band_fill(const Line& line, const Out& out, const BandSmem& sm, int lg, int SEGW,
+                          int lane, uint32_t nem, const unsigned char* full, int a, int b)
+{
+    int cur = -1, fo = 0, featcur = -1, nxt = -1, fnxt = 0, featnxt = -1;
+    bool need_next = false;
+    HullCursor hc{0, 0, 0u};
+    if (nem) {
+        cur = band_prev(sm, lg, SEGW, lane, nem, a);   // last member before a
+        if (cur < 0) cur = sm.lo[(__ffs(nem) - 1) * 32 + lane];
+        line.eval(cur, fo);
+        for (;;) {  // walk left while strictly better at a
+            const int p = band_prev(sm, lg, SEGW, lane, nem, cur);
+            if (p < 0) break;
+            int fp;
+            line.eval(p, fp);
+            if ((long long)fp + (long long)(a - p) * (a - p) <
+                (long long)fo + (long long)(a - cur) * (a - cur)) {
+                cur = p;
+                fo = fp;
+            } else {
+                break;
+            }
+        }
+        line.eval2(cur, fo, featcur);
+        need_next = true;
+    }
+    const int nq = (b - a + OC - 1) / OC;
+    for (int q = 0; q < nq; ++q) {
+        int v[OC], ft[OC];
+        const int j0 = a + q * OC;
+        if (full && j0 + OC <= b && full[j0 >> 5] && cur >= 0) {
+            // every line is a source at every position of this chunk
+#pragma unroll
+            for (int t = 0; t < OC; ++t) {
+                v[t] = 0;
+                ft[t] = line.self_feature(j0 + t);
+            }
+            cur = j0 + OC - 1;
+            fo = 0;
+            featcur = ft[OC - 1];
+            need_next = true;
+        } else {
+#pragma unroll
+            for (int t = 0; t < OC; ++t) {
+                const int j = j0 + t;
+                v[t] = INT32_MAX;
+                ft[t] = -1;
+                if (j < b && cur >= 0) {
+                    if (line.is_zero(j)) {
+                        cur = j;
+                        fo = 0;
+                        featcur = line.self_feature(j);
+                        need_next = true;
+                        v[t] = 0;
+                        ft[t] = featcur;
+                        continue;
+                    }
+                    if (need_next) {
+                        cursor_at(hc, sm, lg, SEGW, lane, cur);
+                        nxt = cursor_next(hc, sm, lg, SEGW, lane, nem);
+                        if (nxt >= 0) line.eval2(nxt, fnxt, featnxt);
+                        need_next = false;
+                    }
+                    while (nxt >= 0 && fnxt + (j - nxt) * (j - nxt) <= fo + (j - cur) * (j - cur)) {
+                        cur = nxt;
+                        fo = fnxt;
+                        featcur = featnxt;
+                        nxt = cursor_next(hc, sm, lg, SEGW, lane, nem);
+                        if (nxt >= 0) line.eval2(nxt, fnxt, featnxt);
+                    }
+                    v[t] = fo + (j - cur) * (j - cur);
+                    ft[t] = featcur;
+                }
+            }
+        }
+        out.store(j0, min(OC, b - j0), v, ft);
+    }
+}
+
 // The whole per-block computation, called by every thread of the block
 // (blockDim.x = 32 * NW, or the NW warps of one group).  Line (per lane) must
 // provide
@@ -555,6 +652,7 @@ __device__ void band_envelope(const Line& line, const Out& out, const BandSmem& 
     }
     sm.lo[warp * 32 + lane] = first;
     sm.hi[warp * 32 + lane] = top;
+    if (warp == 0 && lane == 0) *sm.ctr = 0;
     sync();
 
     // (2) merge segments 1+1, 2+2, ...
@@ -564,85 +662,19 @@ __device__ void band_envelope(const Line& line, const Out& out, const BandSmem& 
         sync();
     }
 
-    // (3) fill.  cur = owner of the current position with value fcur + (j -
-    // cur)^2 and feature featcur; nxt = the next hull member (fnxt, featnxt).
-    // A source position owns itself (value 0); after a run of sources the walk
-    // resumes from the last source of the run.
+    // (3) fill, in units of positions that the warps take in turn from a
+    // shared counter, so that the costly parts of the lines do not leave the
+    // other warps waiting.
     uint32_t nem = 0;
     for (int w = 0; w < NW; ++w) nem |= (uint32_t)(sm.lo[w * 32 + lane] >= 0) << w;
-    int cur = -1, fo = 0, featcur = -1, nxt = -1, fnxt = 0, featnxt = -1;
-    bool need_next = false;
-    HullCursor hc{0, 0, 0u};
-    if (nem && s0 < s1) {
-        const uint32_t before = nem & ((1u << warp) - 1u);
-        cur = before ? sm.hi[(31 - __clz(before)) * 32 + lane] : sm.lo[(__ffs(nem) - 1) * 32 + lane];
-        line.eval(cur, fo);
-        for (;;) {  // walk left while strictly better at s0
-            const int p = band_prev(sm, lg, SEGW, lane, nem, cur);
-            if (p < 0) break;
-            int fp;
-            line.eval(p, fp);
-            if ((long long)fp + (long long)(s0 - p) * (s0 - p) <
-                (long long)fo + (long long)(s0 - cur) * (s0 - cur)) {
-                cur = p;
-                fo = fp;
-            } else {
-                break;
-            }
-        }
-        line.eval2(cur, fo, featcur);
-        need_next = true;
-    }
-    const int nq = ((1 << lg) + OC - 1) / OC;
-    for (int q = 0; q < nq; ++q) {
-        int v[OC], ft[OC];
-        const int j0 = s0 + q * OC;
-        if (full && j0 + OC <= s1 && full[j0 >> 5] && cur >= 0) {
-            // every line is a source at every position of this chunk
-#pragma unroll
-            for (int t = 0; t < OC; ++t) {
-                v[t] = 0;
-                ft[t] = line.self_feature(j0 + t);
-            }
-            cur = j0 + OC - 1;
-            fo = 0;
-            featcur = ft[OC - 1];
-            need_next = true;
-        } else {
-#pragma unroll
-            for (int t = 0; t < OC; ++t) {
-                const int j = j0 + t;
-                v[t] = INT32_MAX;
-                ft[t] = -1;
-                if (j < s1 && cur >= 0) {
-                    if (line.is_zero(j)) {
-                        cur = j;
-                        fo = 0;
-                        featcur = line.self_feature(j);
-                        need_next = true;
-                        v[t] = 0;
-                        ft[t] = featcur;
-                        continue;
-                    }
-                    if (need_next) {
-                        cursor_at(hc, sm, lg, SEGW, lane, cur);
-                        nxt = cursor_next(hc, sm, lg, SEGW, lane, nem);
-                        if (nxt >= 0) line.eval2(nxt, fnxt, featnxt);
-                        need_next = false;
-                    }
-                    while (nxt >= 0 && fnxt + (j - nxt) * (j - nxt) <= fo + (j - cur) * (j - cur)) {
-                        cur = nxt;
-                        fo = fnxt;
-                        featcur = featnxt;
-                        nxt = cursor_next(hc, sm, lg, SEGW, lane, nem);
-                        if (nxt >= 0) line.eval2(nxt, fnxt, featnxt);
-                    }
-                    v[t] = fo + (j - cur) * (j - cur);
-                    ft[t] = featcur;
-                }
-            }
-        }
-        out.store(s0 + q * OC, min(OC, s1 - (s0 + q * OC)), v, ft);
+    const int UL = band_fill_unit(n, NW);
+    const int nunits = (n + UL - 1) / UL;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(sm.ctr, 1);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= nunits) break;
+        band_fill(line, out, sm, lg, SEGW, lane, nem, full, u * UL, min(n, u * UL + UL));
     }
     out.finish();
 }

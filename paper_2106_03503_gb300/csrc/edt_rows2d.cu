@@ -181,9 +181,10 @@ k_rows2d(int H, int W, int nb, RowJob J0, RowJob J1, int lg, int NW,
     uint32_t* sbits = reinterpret_cast<uint32_t*>(smem);
     uint32_t* supdn = sbits + W;
     unsigned char* sfull = reinterpret_cast<unsigned char*>(supdn + W);
-    // TMA staging must start on a 128-byte boundary
-    unsigned char* stage0 = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem + band2d_col_bytes(W)) + 127) & ~uintptr_t(127));
+    // TMA staging starts on a 128-byte boundary (the launch adds 128 bytes
+    // of room for that); without TMA the engine follows the column data
+    unsigned char* stage0 = smem + band2d_col_bytes(W);
+    if (TMA) stage0 = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(stage0) + 127) & ~uintptr_t(127));
     const BandSmem sm = carve_band_smem(stage0 + (TMA ? NW * TMA_STAGE_BYTES : 0), NW, (1 << lg) >> 5);
     const bool second = (int)blockIdx.x >= nb;
     const RowJob& J = second ? J1 : J0;

@@ -48,6 +48,13 @@ struct LineY {
         return true;
     }
     __device__ __forceinline__ bool is_zero(int k) const { return gz[k * 32 + lane] == z; }
+    __device__ __forceinline__ bool chunk_has_source(int j0) const
+    {
+        bool any = false;
+#pragma unroll
+        for (int t = 0; t < OC; ++t) any |= gz[(j0 + t) * 32 + lane] == z;
+        return any;
+    }
     __device__ __forceinline__ int self_feature(int k) const
     {
         return (int)(((uint32_t)z << 16) | (uint32_t)k);
@@ -146,6 +153,13 @@ struct LineX {
         return true;
     }
     __device__ __forceinline__ bool is_zero(int k) const { return rec[k] == self; }
+    __device__ __forceinline__ bool chunk_has_source(int j0) const
+    {
+        bool any = false;
+#pragma unroll
+        for (int t = 0; t < OC; ++t) any |= rec[j0 + t] == self;
+        return any;
+    }
     __device__ __forceinline__ int self_feature(int k) const { return (z * H + y) * W + k; }
 };
 

@@ -486,7 +486,11 @@ __device__ void band_fill(const Line& line, const Out& out, const BandSmem& sm, 
     for (int q = 0; q < nq; ++q) {
         int v[OC], ft[OC];
         const int j0 = a + q * OC;
-        if (full && j0 + OC <= b && full[j0 >> 5] && cur >= 0) {
+        const bool bulk = full && j0 + OC <= b && full[j0 >> 5] && cur >= 0;
+        // whole chunk and no line (of those not in the bulk case) has a source
+        // in it; every lane takes part in the vote
+        const bool clear = j0 + OC <= b && !__any_sync(FULL, !bulk && cur >= 0 && line.chunk_has_source(j0));
+        if (bulk) {
             // every line is a source at every position of this chunk
 #pragma unroll
             for (int t = 0; t < OC; ++t) {
@@ -497,6 +501,49 @@ __device__ void band_fill(const Line& line, const Out& out, const BandSmem& sm, 
             fo = 0;
             featcur = ft[OC - 1];
             need_next = true;
+        } else if (clear) {
+            // no line has a source in this chunk: start from the owner at j0
+            // and take the minimum with every later hull member that beats
+            // (or ties) its predecessor at the chunk's last position -- the
+            // owners of the chunk's positions are exactly those members, and
+            // visiting them left to right with "<=" keeps the rightmost owner
+            // at a tie, as the walk below does
+#pragma unroll
+            for (int t = 0; t < OC; ++t) {
+                v[t] = INT32_MAX;
+                ft[t] = -1;
+            }
+            if (cur >= 0) {
+                if (need_next) {
+                    cursor_at(hc, sm, lg, SEGW, lane, cur);
+                    nxt = cursor_next(hc, sm, lg, SEGW, lane, nem);
+                    if (nxt >= 0) line.eval2(nxt, fnxt, featnxt);
+                    need_next = false;
+                }
+#pragma unroll
+                for (int t = 0; t < OC; ++t) {
+                    const int d = j0 + t - cur;
+                    v[t] = fo + d * d;
+                    ft[t] = featcur;
+                }
+                const int je = j0 + OC - 1;
+                while (nxt >= 0 && fnxt + (je - nxt) * (je - nxt) <= fo + (je - cur) * (je - cur)) {
+#pragma unroll
+                    for (int t = 0; t < OC; ++t) {
+                        const int d = j0 + t - nxt;
+                        const int val = fnxt + d * d;
+                        if (val <= v[t]) {
+                            v[t] = val;
+                            ft[t] = featnxt;
+                        }
+                    }
+                    cur = nxt;
+                    fo = fnxt;
+                    featcur = featnxt;
+                    nxt = cursor_next(hc, sm, lg, SEGW, lane, nem);
+                    if (nxt >= 0) line.eval2(nxt, fnxt, featnxt);
+                }
+            }
         } else {
 #pragma unroll
             for (int t = 0; t < OC; ++t) {
@@ -542,6 +589,7 @@ __device__ void band_fill(const Line& line, const Out& out, const BandSmem& sm, 
 //   bool eval2(int k, int& f, int& g) const   f(k) and the feature of position k
 //   int  c(int k) const                  f(k) + k*k for a finite position
 //   bool is_zero(int k) const            f(k) == 0: position k is a source itself
+//   bool chunk_has_source(int j0) const  is_zero(k) for some k in j0 .. j0+OC-1
 //   int  self_feature(int k) const       feature of a source position k
 // and Out must provide store(int j0, int cnt, const int* v, const int* f),
 // called by every lane of the warp at the same time with the values of its

@@ -71,6 +71,13 @@ struct BandRow2D {
         return true;
     }
     __device__ __forceinline__ bool is_zero(int k) const { return (bits[k] & rbit) != 0u; }
+    __device__ __forceinline__ bool chunk_has_source(int j0) const
+    {
+        // j0 is a multiple of 8 and bits 16-byte aligned
+        const uint4 a = *reinterpret_cast<const uint4*>(bits + j0);
+        const uint4 b = *reinterpret_cast<const uint4*>(bits + j0 + 4);
+        return ((a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w) & rbit) != 0u;
+    }
     __device__ __forceinline__ int self_feature(int k) const { return i * W + k; }
 };
 

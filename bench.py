@@ -12,8 +12,8 @@ map F.  2 * 8192^2 pixels per step.
 Prints one JSON line (rank 0).  `value` is whole-job Gpixel/s over the timed
 steps (CUDA events on the launching stream, L2 flushed between steps by
 writing a 256 MiB buffer, inputs resident in HBM).  `e2e` is the same metric
-through edt_feature_host with pinned host buffers (copies in the timed
-region).  The step calls edt_feature_pair: one column pass and one row-pass
+through edt_feature_pair_host with pinned host buffers (the mask copy and the
+result copies in the timed region).  The step calls edt_feature_pair: one column pass and one row-pass
 launch serve both transforms.  `roofline` is the row-pass kernel k_rows2d, timed live by libedt's
 event tracing, against the measured HBM copy bandwidth.  `cpu_baseline` is the
 CPU oracle timed on this host on one full step.  With --impl reference the
@@ -429,14 +429,13 @@ def run_gpu(args, rank, world, local_rank):
     hD = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
     hF = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
     e2e_steps = max(3, min(args.steps, 20))
-    for mode in (0, 1):
-        edt.feature_host(hmask, mode, D=hD[mode], F=hF[mode])
+    host_out = ((hD[0], hF[0]), (hD[1], hF[1]))
+    edt.feature_pair_host(hmask, out=host_out)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for mode in (0, 1):
-            edt.feature_host(hmask, mode, D=hD[mode], F=hF[mode])
+        edt.feature_pair_host(hmask, out=host_out)
     torch.cuda.synchronize()
     e2e_value, _ = whole_job_rate(1e3 * (time.perf_counter() - t0), px_step, e2e_steps, world,
                                   reduce_max)
@@ -487,9 +486,9 @@ def run_gpu(args, rank, world, local_rank):
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "one full step (both transforms of the 8192x8192 discs "
                                        f"mask), single-threaded C oracle, {cpu_s:.1f} s"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * H * W,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": H * W,
                     "d2h_bytes_per_step": 2 * 2 * 4 * H * W, "steps": e2e_steps,
-                    "api": "edt_feature_host, pinned host buffers"},
+                    "api": "edt_feature_pair_host, pinned host buffers"},
             "gpu_launches": k1_n + k2_n,
             "clocks": clocks,
             "extras": extras,

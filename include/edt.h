@@ -98,10 +98,20 @@ edt_status edt_feature_pair(const uint8_t *mask, int ndim, const int *shape,
  * pointers (pinned memory gives the fastest copies; pageable works).  The
  * call copies the mask to the device, runs the transform, copies the
  * results back and returns when they are in the host buffers.  Device
- * buffers come from the stream-ordered pool of the current device. */
+ * buffers come from the stream-ordered pool of the current device.  For 2-D
+ * images the row pass runs in up to four launches over consecutive bands and
+ * the rows of each go back to the host (on a copy stream of libedt's own)
+ * while the next launch runs. */
 edt_status edt_feature_host(const uint8_t *mask, int ndim, const int *shape,
                             int mode, int32_t *D, int32_t *F, float *dist,
                             edt_stream_t stream);
+
+/* edt_feature_pair with HOST buffers (the mask is copied to the device once
+ * for both transforms), in the manner of edt_feature_host.  F_obj and F_bg
+ * are required, D_obj and D_bg may be NULL. */
+edt_status edt_feature_pair_host(const uint8_t *mask, int ndim, const int *shape,
+                                 int32_t *D_obj, int32_t *F_obj, int32_t *D_bg,
+                                 int32_t *F_bg, edt_stream_t stream);
 
 /* One transform in a batch.  Pointers are device memory; F required, D and
  * dist may be NULL; shape[2] is ignored for ndim = 2. */

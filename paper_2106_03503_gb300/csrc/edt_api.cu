@@ -1,5 +1,6 @@
 // C ABI of libedt: validation, scratch management and dispatch of the plain
 // (one transform per call) entry points declared in include/edt.h.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -38,6 +39,7 @@ void clear_error() { g_err.clear(); }
 struct DeviceInfo {
     std::atomic<int> ready{0};
     int sm_count = 0;
+    cudaStream_t copy = nullptr;   // device-to-host copies of the host-buffer calls
 };
 static DeviceInfo g_dev[64];
 static std::mutex g_dev_mu;
@@ -64,6 +66,8 @@ edt_status device_setup(int* sm_count)
                 uint64_t keep = UINT64_MAX;
                 cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
             }
+            if ((e = cudaStreamCreateWithFlags(&d.copy, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamCreate");
             d.sm_count = sms;
             d.ready.store(1, std::memory_order_release);
         }
@@ -73,6 +77,14 @@ edt_status device_setup(int* sm_count)
 }
 
 // Shape checks shared by every entry point (limits documented in edt.h).
+// Copy stream of the current device (device_setup must have run).
+static cudaStream_t copy_stream()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_dev[dev].copy;
+}
+
 edt_status check_shape(int ndim, const int* shape, int mode)
 {
     if (!shape) return fail(EDT_ERR_INVALID, "shape is NULL");
@@ -210,6 +222,127 @@ edt_status plain_call(const uint8_t* mask, int ndim, const int* shape, int mode,
     return st;
 }
 
+// --- host-buffer calls --------------------------------------------------------
+
+// One transform's host result buffers (D and dist may be NULL).
+struct HostOut {
+    int mode;
+    int32_t* D;
+    int32_t* F;
+    float* dist;
+};
+
+// Copy the mask to the device, run one transform (nout = 1) or both
+// transforms of the mask (nout = 2, modes 0 and 1), copy the results back
+// and wait for them.  For 2-D images the row pass runs in up to four launches
+// over consecutive band ranges, and the rows of each range go back to the
+// host on the device's copy stream as soon as its launch has finished, so
+// that the device-to-host copy -- the bottleneck: 4 to 12 bytes per pixel and
+// transform over the host link -- overlaps the rest of the row pass.
+edt_status host_call(const uint8_t* mask, int ndim, const int* shape, const HostOut* outs, int nout,
+                     cudaStream_t stream)
+{
+    int64_t n = 1;
+    for (int a = 0; a < ndim; ++a) n *= shape[a];
+    int sms = 0;
+    edt_status st = device_setup(&sms);
+    if (st != EDT_OK) return st;
+    // one device block: mask | per transform D, F, dist | scratch per transform
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t bx = al(scratch_bytes(ndim, shape));
+    size_t total = al((size_t)n) + nout * bx;
+    for (int k = 0; k < nout; ++k)
+        total += (outs[k].D ? al((size_t)n * 4) : 0) + al((size_t)n * 4) + (outs[k].dist ? al((size_t)n * 4) : 0);
+    char* dev = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&dev, total, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    char* p = dev;
+    uint8_t* dmask = reinterpret_cast<uint8_t*>(p);
+    p += al((size_t)n);
+    int32_t* dD[2] = {nullptr, nullptr};
+    int32_t* dF[2] = {nullptr, nullptr};
+    float* dS[2] = {nullptr, nullptr};
+    void* scr[2] = {nullptr, nullptr};
+    for (int k = 0; k < nout; ++k) {
+        if (outs[k].D) { dD[k] = reinterpret_cast<int32_t*>(p); p += al((size_t)n * 4); }
+        dF[k] = reinterpret_cast<int32_t*>(p);
+        p += al((size_t)n * 4);
+        if (outs[k].dist) { dS[k] = reinterpret_cast<float*>(p); p += al((size_t)n * 4); }
+        scr[k] = p;
+        p += bx;
+    }
+    cudaStream_t cs = copy_stream();
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (auto& x : ev)
+        if (st == EDT_OK && (e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess)
+            st = cuda_fail(e, "cudaEventCreate");
+    if (st == EDT_OK && (e = cudaMemcpyAsync(dmask, mask, (size_t)n, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        st = cuda_fail(e, "cudaMemcpyAsync H2D");
+    // rows [r0, r1) of every result, device to host, on `on`
+    auto copy_rows = [&](int64_t r0, int64_t r1, int64_t row, cudaStream_t on) {
+        const size_t off = (size_t)(r0 * row), cnt = (size_t)((r1 - r0) * row) * 4;
+        for (int k = 0; k < nout && st == EDT_OK; ++k) {
+            if (outs[k].D && (e = cudaMemcpyAsync(outs[k].D + off, dD[k] + off, cnt, cudaMemcpyDeviceToHost, on)) != cudaSuccess)
+                st = cuda_fail(e, "cudaMemcpyAsync D2H");
+            if (st == EDT_OK &&
+                (e = cudaMemcpyAsync(outs[k].F + off, dF[k] + off, cnt, cudaMemcpyDeviceToHost, on)) != cudaSuccess)
+                st = cuda_fail(e, "cudaMemcpyAsync D2H");
+            if (st == EDT_OK && outs[k].dist &&
+                (e = cudaMemcpyAsync(outs[k].dist + off, dS[k] + off, cnt, cudaMemcpyDeviceToHost, on)) != cudaSuccess)
+                st = cuda_fail(e, "cudaMemcpyAsync D2H");
+        }
+    };
+    bool used_cs = false, joined = false;
+    if (st == EDT_OK && ndim == 2) {
+        const int H = shape[0], W = shape[1];
+        const ColGeom g = col_geom(H, W);
+        const ColScratch s0 = col_scratch_carve(scr[0], g);
+        const ColScratch s1 = nout == 2 ? col_scratch_carve(scr[1], g) : s0;
+        if ((e = cudaMemsetAsync(s0.cnt, 0, (size_t)g.ntiles * 4, stream)) != cudaSuccess)
+            st = cuda_fail(e, "cudaMemsetAsync");
+        if (st == EDT_OK &&
+            (e = traced("k_colbits", stream, [&] {
+                 return nout == 2 ? launch_colbits_pair(dmask, g, s0, s1, stream)
+                                  : launch_colbits(dmask, g, outs[0].mode, s0, stream);
+             })) != cudaSuccess)
+            st = cuda_fail(e, "column pass launch");
+        const int nchunk = g.nb >= 16 ? 4 : 1;
+        for (int c = 0; c < nchunk && st == EDT_OK; ++c) {
+            const int b0 = (int)((int64_t)g.nb * c / nchunk), b1 = (int)((int64_t)g.nb * (c + 1) / nchunk);
+            e = traced("k_rows2d", stream, [&] {
+                return nout == 2 ? launch_rows2d_pair(H, W, g, s0, s1, dD[0], dF[0], dD[1], dF[1], stream, b0, b1 - b0)
+                                 : launch_rows2d(H, W, g, s0, dD[0], dF[0], dS[0], sms, stream, b0, b1 - b0);
+            });
+            if (e != cudaSuccess) { st = cuda_fail(e, "row pass launch"); break; }
+            if ((e = cudaEventRecord(ev[c], stream)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev[c], 0)) != cudaSuccess) {
+                st = cuda_fail(e, "event");
+                break;
+            }
+            used_cs = true;
+            copy_rows((int64_t)b0 * 32, std::min<int64_t>((int64_t)b1 * 32, H), W, cs);
+        }
+        // order the free below after the copies
+        if (st == EDT_OK) {
+            if ((e = cudaEventRecord(ev[4], cs)) != cudaSuccess || (e = cudaStreamWaitEvent(stream, ev[4], 0)) != cudaSuccess)
+                st = cuda_fail(e, "event");
+            else
+                joined = true;
+        }
+    } else if (st == EDT_OK) {
+        for (int k = 0; k < nout && st == EDT_OK; ++k)
+            st = run_transform(dmask, ndim, shape, outs[k].mode, dD[k], dF[k], dS[k], scr[k], sms, stream);
+        if (st == EDT_OK) copy_rows(0, n / shape[ndim - 1], shape[ndim - 1], stream);
+    }
+    if (used_cs && !joined) cudaStreamSynchronize(cs);   // after an error: no copy may outlive the block
+    cudaFreeAsync(dev, stream);
+    e = cudaStreamSynchronize(stream);
+    if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    if (st == EDT_OK) clear_error();
+    return st;
+}
+
 }  // namespace edt
 
 using namespace edt;
@@ -281,47 +414,23 @@ edt_status edt_feature_pair(const uint8_t* mask, int ndim, const int* shape, int
 
 edt_status edt_feature_host(const uint8_t* mask, int ndim, const int* shape,
                             int mode, int32_t* D, int32_t* F, float* dist,
-                            edt_stream_t stream_)
+                            edt_stream_t stream)
 {
-    cudaStream_t stream = (cudaStream_t)stream_;
     edt_status st = check_shape(ndim, shape, mode);
     if (st != EDT_OK) return st;
     if (!mask || !F) return fail(EDT_ERR_INVALID, "mask and F must not be NULL");
-    int64_t n = 1;
-    for (int a = 0; a < ndim; ++a) n *= shape[a];
-    int sms = 0;
-    if ((st = device_setup(&sms)) != EDT_OK) return st;
-    // one device block: mask | D | F | dist | scratch, 256-byte aligned parts
-    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t bm = al((size_t)n), bd = D ? al((size_t)n * 4) : 0, bf = al((size_t)n * 4),
-                 bs = dist ? al((size_t)n * 4) : 0, bx = scratch_bytes(ndim, shape);
-    char* dev = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&dev, bm + bd + bf + bs + bx, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
-    uint8_t* dmask = reinterpret_cast<uint8_t*>(dev);
-    int32_t* dD = D ? reinterpret_cast<int32_t*>(dev + bm) : nullptr;
-    int32_t* dF = reinterpret_cast<int32_t*>(dev + bm + bd);
-    float* dS = dist ? reinterpret_cast<float*>(dev + bm + bd + bf) : nullptr;
-    void* scratch = dev + bm + bd + bf + bs;
-    st = EDT_OK;
-    if ((e = cudaMemcpyAsync(dmask, mask, (size_t)n, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-        st = cuda_fail(e, "cudaMemcpyAsync H2D");
-    if (st == EDT_OK)
-        st = run_transform(dmask, ndim, shape, mode, dD, dF, dS, scratch, sms, stream);
-    if (st == EDT_OK && D &&
-        (e = cudaMemcpyAsync(D, dD, (size_t)n * 4, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-        st = cuda_fail(e, "cudaMemcpyAsync D2H");
-    if (st == EDT_OK &&
-        (e = cudaMemcpyAsync(F, dF, (size_t)n * 4, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-        st = cuda_fail(e, "cudaMemcpyAsync D2H");
-    if (st == EDT_OK && dist &&
-        (e = cudaMemcpyAsync(dist, dS, (size_t)n * 4, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-        st = cuda_fail(e, "cudaMemcpyAsync D2H");
-    cudaFreeAsync(dev, stream);
-    e = cudaStreamSynchronize(stream);
-    if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
-    if (st == EDT_OK) clear_error();
-    return st;
+    const HostOut out{mode, D, F, dist};
+    return host_call(mask, ndim, shape, &out, 1, (cudaStream_t)stream);
+}
+
+edt_status edt_feature_pair_host(const uint8_t* mask, int ndim, const int* shape, int32_t* D_obj,
+                                 int32_t* F_obj, int32_t* D_bg, int32_t* F_bg, edt_stream_t stream)
+{
+    edt_status st = check_shape(ndim, shape, EDT_TO_OBJECT);
+    if (st != EDT_OK) return st;
+    if (!mask || !F_obj || !F_bg) return fail(EDT_ERR_INVALID, "mask, F_obj and F_bg must not be NULL");
+    const HostOut outs[2] = {{EDT_TO_OBJECT, D_obj, F_obj, nullptr}, {EDT_TO_BACKGROUND, D_bg, F_bg, nullptr}};
+    return host_call(mask, ndim, shape, outs, 2, (cudaStream_t)stream);
 }
 
 edt_status edt_trace_enable(int on)

@@ -42,14 +42,16 @@ ColScratch col_scratch_carve(void* base, const ColGeom& g);
 // Launchers (asynchronous on `stream`; return cudaGetLastError()).
 cudaError_t launch_colbits(const uint8_t* mask, const ColGeom& g, int mode,
                            const ColScratch& s, cudaStream_t stream);
+// Row pass over bands [band0, band0 + nbl) (nbl < 0: to the last band).
 cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
                           int32_t* D, int32_t* F, float* dist, int sm_count,
-                          cudaStream_t stream);
+                          cudaStream_t stream, int band0 = 0, int nbl = -1);
 cudaError_t launch_colbits_pair(const uint8_t* mask, const ColGeom& g, const ColScratch& s,
                                 const ColScratch& s1, cudaStream_t stream);
 cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch& s_obj,
                                const ColScratch& s_bg, int32_t* D_obj, int32_t* F_obj,
-                               int32_t* D_bg, int32_t* F_bg, cudaStream_t stream);
+                               int32_t* D_bg, int32_t* F_bg, cudaStream_t stream, int band0 = 0,
+                               int nbl = -1);
 cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
                            const ColScratch& s, uint32_t* P, cudaStream_t stream);
 cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,

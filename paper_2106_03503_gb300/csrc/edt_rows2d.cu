@@ -175,11 +175,12 @@ struct RowJob {
     float* dist;
 };
 
-// Blocks [0, nb) run job 0, blocks [nb, 2 nb) job 1 (when two transforms of
-// one mask are fused); one block per band of 32 rows.
+// One block per band of 32 rows, bands band0 .. band0 + nbl - 1: blocks
+// [0, nbl) run job 0, blocks [nbl, 2 nbl) job 1 (when two transforms of one
+// mask are fused).
 template <bool TMA>
 __global__ void __launch_bounds__(512, 2)
-k_rows2d(int H, int W, int nb, RowJob J0, RowJob J1, int lg, int NW,
+k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
          const __grid_constant__ CUtensorMap mD0, const __grid_constant__ CUtensorMap mF0,
          const __grid_constant__ CUtensorMap mS0, const __grid_constant__ CUtensorMap mD1,
          const __grid_constant__ CUtensorMap mF1, const __grid_constant__ CUtensorMap mS1)
@@ -193,9 +194,9 @@ k_rows2d(int H, int W, int nb, RowJob J0, RowJob J1, int lg, int NW,
     unsigned char* stage0 = smem + band2d_col_bytes(W);
     if (TMA) stage0 = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(stage0) + 127) & ~uintptr_t(127));
     const BandSmem sm = carve_band_smem(stage0 + (TMA ? NW * TMA_STAGE_BYTES : 0), NW, (1 << lg) >> 5);
-    const bool second = (int)blockIdx.x >= nb;
+    const bool second = (int)blockIdx.x >= nbl;
     const RowJob& J = second ? J1 : J0;
-    const int b = second ? (int)blockIdx.x - nb : (int)blockIdx.x;
+    const int b = band0 + (second ? (int)blockIdx.x - nbl : (int)blockIdx.x);
     stage_band(J.s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x, J.invert != 0);
     __syncthreads();
 
@@ -223,8 +224,9 @@ k_rows2d(int H, int W, int nb, RowJob J0, RowJob J1, int lg, int NW,
     }
 }
 
-// Row pass for one transform (J1 unused) or two transforms of one mask.
-static cudaError_t launch_rows(int H, int W, const ColGeom& g, const RowJob& J0, const RowJob* J1,
+// Row pass over bands [band0, band0 + nbl) for one transform (J1 unused) or
+// two transforms of one mask.
+static cudaError_t launch_rows(int H, int W, const RowJob& J0, const RowJob* J1, int band0, int nbl,
                                cudaStream_t stream)
 {
     CUtensorMap m[6];
@@ -247,35 +249,36 @@ static cudaError_t launch_rows(int H, int W, const ColGeom& g, const RowJob& J0,
         smem = band2d_smem(W, lg, NW) + (tma ? NW * TMA_STAGE_BYTES + 128 : 0);
         if (smem <= 227 * 1024) break;
     }
+    if (nbl <= 0) return cudaSuccess;
     const RowJob j1 = J1 ? *J1 : J0;
-    const unsigned blocks = (unsigned)(g.nb * (J1 ? 2 : 1));
+    const unsigned blocks = (unsigned)(nbl * (J1 ? 2 : 1));
     if (tma)
-        k_rows2d<true><<<blocks, NW * 32, smem, stream>>>(H, W, g.nb, J0, j1, lg, NW, m[0], m[1], m[2], m[3],
-                                                          m[4], m[5]);
+        k_rows2d<true><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1], m[2],
+                                                          m[3], m[4], m[5]);
     else
-        k_rows2d<false><<<blocks, NW * 32, smem, stream>>>(H, W, g.nb, J0, j1, lg, NW, m[0], m[1], m[2], m[3],
-                                                           m[4], m[5]);
+        k_rows2d<false><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1], m[2],
+                                                           m[3], m[4], m[5]);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rows2d(int H, int W, const ColGeom& g, const ColScratch& s,
                           int32_t* D, int32_t* F, float* dist, int sm_count,
-                          cudaStream_t stream)
+                          cudaStream_t stream, int band0, int nbl)
 {
     (void)sm_count;
     const RowJob J{s, 0, D, F, dist};
-    return launch_rows(H, W, g, J, nullptr, stream);
+    return launch_rows(H, W, J, nullptr, band0, nbl < 0 ? g.nb - band0 : nbl, stream);
 }
 
 cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch& s_obj,
                                const ColScratch& s_bg, int32_t* D_obj, int32_t* F_obj,
-                               int32_t* D_bg, int32_t* F_bg, cudaStream_t stream)
+                               int32_t* D_bg, int32_t* F_bg, cudaStream_t stream, int band0, int nbl)
 {
     ColScratch sb = s_bg;
     sb.C = s_obj.C;   // the to-background sources are the complement of these words
     const RowJob J0{s_obj, 0, D_obj, F_obj, nullptr};
     const RowJob J1{sb, 1, D_bg, F_bg, nullptr};
-    return launch_rows(H, W, g, J0, &J1, stream);
+    return launch_rows(H, W, J0, &J1, band0, nbl < 0 ? g.nb - band0 : nbl, stream);
 }
 
 // --- batched row pass -------------------------------------------------------

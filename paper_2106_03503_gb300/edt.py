@@ -56,6 +56,7 @@ _lib.edt_sq3d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.
 _lib.edt_feature.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.edt_feature_host.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.edt_feature_pair.argtypes = [_vp, ctypes.c_int, _i32p, _vp, _vp, _vp, _vp, _vp]
+_lib.edt_feature_pair_host.argtypes = [_vp, ctypes.c_int, _i32p, _vp, _vp, _vp, _vp, _vp]
 _lib.edt_trace_enable.argtypes = [ctypes.c_int]
 _lib.edt_trace_enable.restype = ctypes.c_int
 _lib.edt_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -66,7 +67,8 @@ _lib.edt_version.restype = ctypes.c_char_p
 for _name in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host", "edt_feature_pair"):
     getattr(_lib, _name).restype = ctypes.c_int
 
-EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_pair", "edt_feature_host", "edt_plan_create",
+EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_pair", "edt_feature_host",
+           "edt_feature_pair_host", "edt_plan_create",
            "edt_plan_destroy", "edt_batch", "edt_serve_create", "edt_serve_submit",
            "edt_serve_poll", "edt_serve_destroy", "edt_trace_enable", "edt_trace_read",
            "edt_last_error", "edt_version")
@@ -329,3 +331,25 @@ def feature_host(mask: np.ndarray, mode: int = TO_OBJECT, D=None, F=None, dist=N
     _check(_lib.edt_feature_host(p(m), len(shape), _shape_arr(shape), int(mode), p(D), p(F),
                                  p(dist), _stream_handle(stream)))
     return (D, F, dist) if want_dist else (D, F)
+
+
+def feature_pair_host(mask, out=None, want_D: bool = True, stream=None):
+    """edt_feature_pair_host on host (numpy or pinned torch CPU) buffers:
+    returns ((D_obj, F_obj), (D_bg, F_bg)) filled in place, synchronously."""
+    if isinstance(mask, torch.Tensor):
+        m = mask.contiguous()
+        shape = tuple(m.shape)
+        mk = lambda: torch.empty(shape, dtype=torch.int32, pin_memory=m.is_pinned())  # noqa: E731
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    else:
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        shape = m.shape
+        mk = lambda: np.empty(shape, np.int32)  # noqa: E731
+        p = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    if out is not None:
+        (Do, Fo), (Db, Fb) = out
+    else:
+        Do, Fo, Db, Fb = (mk() if want_D else None), mk(), (mk() if want_D else None), mk()
+    _check(_lib.edt_feature_pair_host(p(m), len(shape), _shape_arr(shape), p(Do), p(Fo), p(Db), p(Fb),
+                                      _stream_handle(stream)))
+    return (Do, Fo), (Db, Fb)

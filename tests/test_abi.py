@@ -24,7 +24,8 @@ def declared():
 
 def test_header_declares_the_interface():
     names = declared()
-    for must in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_batch", "edt_serve_submit",
+    for must in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_pair", "edt_feature_host",
+                 "edt_feature_pair_host", "edt_batch", "edt_serve_submit",
                  "edt_serve_poll", "edt_feature2d_noalloc", "edt_last_error"):
         assert must in names
 
@@ -65,6 +66,15 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
     assert lib.edt_serve_submit(None, None, None) == 1
     lib.edt_feature2d_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
     assert lib.edt_feature2d_noalloc(dummy, 4, 4, 3, dummy, dummy, None, None) == 1
+    for name in ("edt_feature_pair", "edt_feature_pair_host"):
+        fn = getattr(lib, name)
+        fn.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, vp, vp, vp, vp]
+        assert fn(dummy, 2, shape, dummy, dummy, dummy, None, None) == 1        # F_bg missing
+        assert fn(dummy, 2, big, dummy, dummy, dummy, dummy, None) == 2
+    lib.edt_feature_host.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                     vp, vp, vp, vp]
+    assert lib.edt_feature_host(None, 2, shape, 0, dummy, dummy, None, None) == 1
+    assert lib.edt_feature_host(dummy, 2, shape, 9, dummy, dummy, None, None) == 1
 
 
 def test_version_string(lib):

@@ -155,3 +155,29 @@ def test_output_alignments(shape, offset):
     for b in bufs:   # nothing written outside the views
         h = b.cpu().numpy()
         assert not h[:offset].any() and not h[offset + n:].any()
+
+
+@pytest.mark.parametrize("shape", [(5, 7), (100, 300), (513, 1000), (1000, 37), (2049, 2052), (20, 33, 40)])
+def test_host_buffer_calls_match_device_calls(shape):
+    """edt_feature_host and edt_feature_pair_host (host buffers; 2-D row pass
+    in up to four band ranges whose rows are copied back while the next range
+    runs) give the same bits as the device-buffer calls."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    for k, p in enumerate([0.003, 0.3]):
+        m_np = inputs.bernoulli_mask(shape, p, 500 + k)
+        m = torch.from_numpy(m_np).cuda()
+        for mode in (0, 1):
+            Dd, Fd, Sd = edt.feature(m, mode, want_dist=True)
+            Dh, Fh, Sh = edt.feature_host(m_np, mode, want_dist=True)          # pageable numpy
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(Dh, Dd.cpu().numpy())
+            np.testing.assert_array_equal(Fh, Fd.cpu().numpy())
+            np.testing.assert_array_equal(Sh.view(np.uint32), Sd.cpu().numpy().view(np.uint32))
+        (Do, Fo), (Db, Fb) = edt.feature_pair(m)
+        hm = torch.from_numpy(m_np).pin_memory()
+        (hDo, hFo), (hDb, hFb) = edt.feature_pair_host(hm)                     # pinned torch
+        torch.cuda.synchronize()
+        for a, b in ((hDo, Do), (hFo, Fo), (hDb, Db), (hFb, Fb)):
+            assert torch.equal(a, b.cpu())
+        np.testing.assert_array_equal(hDo.numpy(), oracle.edt(m_np, 0)[0])

@@ -1,0 +1,145 @@
+// Driver of the host emulation of libedt's kernels (test infrastructure):
+// runs the 2-D column and row kernels (single transforms and the fused pair)
+// and the 3-D passes on seeded random masks and compares the result with the
+// CPU oracle: D exactly, F a source at squared distance D.
+//   emu 2d PART NPARTS   2-D cases whose index is PART modulo NPARTS
+//   emu 3d               3-D cases
+#include "shim.h"
+#include "src/edt_internal.h"
+extern "C" {
+int oracle_edt2d(const uint8_t* mask, int M, int L, int mode, int32_t* D, int32_t* F);
+int oracle_edt3d(const uint8_t* mask, int Z, int M, int L, int mode, int32_t* D, int32_t* F);
+}
+using namespace edt;
+
+static uint64_t rng_state = 12345;
+static double urand()
+{
+    rng_state = rng_state * 6364136223846793005ULL + 1442695040888963407ULL;
+    return (rng_state >> 11) * (1.0 / 9007199254740992.0);
+}
+
+static int check_features(const std::vector<uint8_t>& mask, int H, int W, int mode, const int32_t* D,
+                          const int32_t* F, const std::vector<int32_t>& Do)
+{
+    int bad = 0;
+    const size_t n = (size_t)H * W;
+    for (size_t i = 0; i < n && bad < 5; ++i) {
+        if (D[i] != Do[i]) {
+            fprintf(stderr, "D mismatch %dx%d mode %d at %zu: %d vs %d\n", H, W, mode, i, D[i], Do[i]);
+            ++bad;
+            continue;
+        }
+        if (Do[i] == INT32_MAX) {
+            if (F[i] != -1) { fprintf(stderr, "F not -1 at %zu\n", i); ++bad; }
+            continue;
+        }
+        const int64_t q = F[i];
+        const bool src = q >= 0 && (size_t)q < n && (mode == 0 ? mask[q] != 0 : mask[q] == 0);
+        const int64_t di = (int64_t)(i / W) - q / W, dj = (int64_t)(i % W) - q % W;
+        if (!src || di * di + dj * dj != Do[i]) { fprintf(stderr, "F invalid %dx%d at %zu\n", H, W, i); ++bad; }
+    }
+    return bad;
+}
+
+static int32_t* alloc_words(size_t n) { return (int32_t*)aligned_alloc(256, (n * 4 + 255) / 256 * 256); }
+
+static int run2d(int H, int W, double p, int mode, int align_off, bool pair)
+{
+    std::vector<uint8_t> mask((size_t)H * W);
+    for (auto& m : mask) m = urand() < p;
+    const ColGeom g = col_geom(H, W);
+    std::vector<unsigned char> sa(col_scratch_bytes(g) + 256), sb(col_scratch_bytes(g) + 256);
+    ColScratch s0 = col_scratch_carve((void*)(((uintptr_t)sa.data() + 255) & ~uintptr_t(255)), g);
+    ColScratch s1 = col_scratch_carve((void*)(((uintptr_t)sb.data() + 255) & ~uintptr_t(255)), g);
+    memset(s0.cnt, 0, g.ntiles * 4);
+    memset(s1.cnt, 0, g.ntiles * 4);
+    const size_t n = (size_t)H * W;
+    // result arrays start align_off words after a 256-byte boundary
+    int32_t* Db = alloc_words(n + align_off);
+    int32_t* Fb = alloc_words(n + align_off);
+    int32_t* Sb = alloc_words(n + align_off);
+    int32_t* D1 = alloc_words(n);
+    int32_t* F1 = alloc_words(n);
+    int32_t *D = Db + align_off, *F = Fb + align_off;
+    float* dist = reinterpret_cast<float*>(Sb + align_off);
+    if (pair) {
+        launch_colbits_pair(mask.data(), g, s0, s1, nullptr);
+        launch_rows2d_pair(H, W, g, s0, s1, D, F, D1, F1, nullptr);
+    } else {
+        launch_colbits(mask.data(), g, mode, s0, nullptr);
+        launch_rows2d(H, W, g, s0, D, F, dist, 0, nullptr);
+    }
+    int bad = 0;
+    for (int k = 0; k < (pair ? 2 : 1); ++k) {
+        const int mm = pair ? k : mode;
+        std::vector<int32_t> Do(n), Fo(n);
+        oracle_edt2d(mask.data(), H, W, mm, Do.data(), Fo.data());
+        bad += check_features(mask, H, W, mm, k ? D1 : D, k ? F1 : F, Do);
+        if (!pair)
+            for (size_t i = 0; i < n && bad < 5; ++i) {
+                const float want = Do[i] == INT32_MAX ? INFINITY : (float)std::sqrt((double)Do[i]);
+                if (memcmp(&dist[i], &want, 4) != 0) { fprintf(stderr, "dist mismatch at %zu\n", i); ++bad; }
+            }
+    }
+    free(Db); free(Fb); free(Sb); free(D1); free(F1);
+    return bad;
+}
+
+static int run3d(int Dz, int H, int W, double p, int mode)
+{
+    std::vector<uint8_t> mask((size_t)Dz * H * W);
+    for (auto& m : mask) m = urand() < p;
+    const ColGeom g = col_geom(Dz, (int64_t)H * W);
+    std::vector<unsigned char> scratch(col_scratch_bytes(g) + 256);
+    ColScratch s = col_scratch_carve((void*)(((uintptr_t)scratch.data() + 255) & ~uintptr_t(255)), g);
+    memset(s.cnt, 0, g.ntiles * 4);
+    const size_t n = mask.size();
+    int32_t* D = alloc_words(n);
+    int32_t* F = alloc_words(n);
+    float* dist = reinterpret_cast<float*>(alloc_words(n));
+    launch_colbits(mask.data(), g, mode, s, nullptr);
+    launch_ypass3d(Dz, H, W, g, s, reinterpret_cast<uint32_t*>(F), nullptr);
+    launch_xpass3d(Dz, H, W, reinterpret_cast<uint32_t*>(F), D, F, dist, nullptr);
+    std::vector<int32_t> Do(n), Fo(n);
+    oracle_edt3d(mask.data(), Dz, H, W, mode, Do.data(), Fo.data());
+    int bad = 0;
+    for (size_t q = 0; q < n && bad < 5; ++q)
+        if (D[q] != Do[q]) { fprintf(stderr, "3-D D mismatch %dx%dx%d at %zu: %d vs %d\n", Dz, H, W, q, D[q], Do[q]); ++bad; }
+    free(D); free(F); free(dist);
+    return bad;
+}
+
+int main(int argc, char** argv)
+{
+    if (argc > 1 && !strcmp(argv[1], "3d")) {
+        int bad = 0, cases = 0;
+        const int shapes[][3] = {{1, 1, 1}, {3, 5, 7}, {1, 40, 50}, {40, 1, 50}, {40, 50, 1},
+                                 {32, 33, 31}, {33, 32, 65}, {70, 17, 129}, {9, 17, 1000}, {5, 300, 40}};
+        for (auto& sh : shapes)
+            for (double p : {0.001, 0.05, 0.5})
+                for (int mode = 0; mode < 2; ++mode) {
+                    bad += run3d(sh[0], sh[1], sh[2], p, mode);
+                    ++cases;
+                }
+        printf("3d cases %d bad %d\n", cases, bad);
+        return bad != 0;
+    }
+    const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
+    const int Hs[] = {1, 2, 33, 64, 100};
+    const int Ws[] = {1, 5, 16, 31, 32, 48, 100, 513, 1024, 2048, 2052, 4100, 8192};
+    const double ps[] = {0.0, 0.001, 0.02, 0.3, 1.0};
+    int cases = 0, run = 0, bad = 0;
+    for (int H : Hs)
+        for (int W : Ws) {
+            if ((long long)H * W > 300000) continue;
+            for (double p : ps) {
+                const int c = cases++;
+                if (c % nparts != part) { for (long long i = 0; i < (long long)H * W; ++i) urand(); continue; }
+                ++run;
+                bad += run2d(H, W, p, c & 1, (c % 3 == 0) ? 4 : ((c % 7 == 0) ? 1 : 0), c % 5 == 0);
+            }
+        }
+    printf("2d cases %d bad %d\n", run, bad);
+    return bad != 0;
+}

@@ -1,4 +1,5 @@
-"""CPU oracle for the exact squared Euclidean distance transform.
+"""CPU oracle for the exact squared Euclidean distance transform (and the
+city-block and chamfer 4-3 transforms of Section 2).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` use this package; the CUDA library and its Python
@@ -28,6 +29,7 @@ INF32 = np.iinfo(np.int32).max
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "edt_oracle.c")
+_SRC_NEDT = os.path.join(_HERE, "nedt_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle_edt.so")
 _lock = threading.Lock()
@@ -38,11 +40,11 @@ def build(force: bool = False) -> str:
     """Compile edt_oracle.c into a shared library (plain gcc, no CUDA)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_NEDT))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                           _SRC, "-o", tmp, "-lm"])
+                           _SRC, _SRC_NEDT, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -72,6 +74,10 @@ def _load():
         lib.oracle_envelope_state.argtypes = [i64p, ctypes.c_long, ctypes.c_int64, i64p, i64p]
         lib.oracle_sqrt_f32.restype = None
         lib.oracle_sqrt_f32.argtypes = [i32p, ctypes.c_long, ctypes.POINTER(ctypes.c_float)]
+        for name in ("oracle_cityblock2d", "oracle_cityblock2d_4scan", "oracle_chamfer43_2d"):
+            fn = getattr(lib, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p]
         _lib = lib
         return lib
 
@@ -161,3 +167,30 @@ def sqrt_f32(D) -> np.ndarray:
     out = np.empty(d.shape, dtype=np.float32)
     lib.oracle_sqrt_f32(_ptr(d, ctypes.c_int32), d.size, _ptr(out, ctypes.c_float))
     return out
+
+
+def _nedt(name, mask, mode, stop):
+    lib = _load()
+    m = _mask(mask)
+    assert m.ndim == 2
+    D = np.empty(m.shape, dtype=np.int32)
+    if getattr(lib, name)(_ptr(m, ctypes.c_uint8), m.shape[0], m.shape[1], int(mode), int(stop),
+                          _ptr(D, ctypes.c_int32)) != 0:
+        raise MemoryError("oracle ran out of memory")
+    return D
+
+
+def cityblock(mask, mode: int = TO_OBJECT, stop_after_forward: bool = False):
+    """City-block distance transform of Sec. 2.1, two raster scans (int32;
+    INT32_MAX where no source is reachable)."""
+    return _nedt("oracle_cityblock2d", mask, mode, stop_after_forward)
+
+
+def cityblock_4scan(mask, mode: int = TO_OBJECT, stop_after_columns: bool = False):
+    """City-block transform of Sec. 2.1 by the four scans (columns, then rows)."""
+    return _nedt("oracle_cityblock2d_4scan", mask, mode, stop_after_columns)
+
+
+def chamfer43(mask, mode: int = TO_OBJECT, stop_after_forward: bool = False):
+    """Chamfer 4-3 distance transform of Sec. 2.2, two raster scans."""
+    return _nedt("oracle_chamfer43_2d", mask, mode, stop_after_forward)

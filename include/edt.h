@@ -113,6 +113,14 @@ edt_status edt_feature_pair_host(const uint8_t *mask, int ndim, const int *shape
                                  int32_t *D_obj, int32_t *F_obj, int32_t *D_bg,
                                  int32_t *F_bg, edt_stream_t stream);
 
+/* City-block distance transform of a 2-D image (Sec. 2.1): D[i][j] = the
+ * smallest |i - a| + |j - b| over the source pixels (a, b) of `mode`,
+ * INT32_MAX when the image has no source.  The same result as the paper's
+ * sequential two-scan and four-scan algorithms.  Device pointers; D is
+ * H x W int32, row-major.  Errors as edt_sq2d. */
+edt_status edt_cityblock2d(const uint8_t *mask, int H, int W, int mode,
+                           int32_t *D, edt_stream_t stream);
+
 /* One transform in a batch.  Pointers are device memory; F required, D and
  * dist may be NULL; shape[2] is ignored for ndim = 2. */
 typedef struct {

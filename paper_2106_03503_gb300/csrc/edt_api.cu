@@ -412,6 +412,35 @@ edt_status edt_feature_pair(const uint8_t* mask, int ndim, const int* shape, int
     return st;
 }
 
+edt_status edt_cityblock2d(const uint8_t* mask, int H, int W, int mode, int32_t* D, edt_stream_t stream_)
+{
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int shape[2] = {H, W};
+    edt_status st = check_shape(2, shape, mode);
+    if (st != EDT_OK) return st;
+    if (!mask || !D) return fail(EDT_ERR_INVALID, "mask and D must not be NULL");
+    int sms = 0;
+    if ((st = device_setup(&sms)) != EDT_OK) return st;
+    const ColGeom g = col_geom(H, W);
+    void* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, col_scratch_bytes(g), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (scratch)");
+    const ColScratch s = col_scratch_carve(scratch, g);
+    if ((e = cudaMemsetAsync(s.cnt, 0, (size_t)g.ntiles * 4, stream)) != cudaSuccess)
+        st = cuda_fail(e, "cudaMemsetAsync");
+    if (st == EDT_OK &&
+        (e = traced("k_colbits", stream, [&] { return launch_colbits(mask, g, mode, s, stream); })) != cudaSuccess)
+        st = cuda_fail(e, "column pass launch");
+    if (st == EDT_OK &&
+        (e = traced("k_cityblock_rows", stream, [&] { return launch_cityblock_rows(H, W, g, s, D, stream); })) !=
+            cudaSuccess)
+        st = cuda_fail(e, "row pass launch");
+    e = cudaFreeAsync(scratch, stream);
+    if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync");
+    if (st == EDT_OK) clear_error();
+    return st;
+}
+
 edt_status edt_feature_host(const uint8_t* mask, int ndim, const int* shape,
                             int mode, int32_t* D, int32_t* F, float* dist,
                             edt_stream_t stream)

@@ -52,6 +52,10 @@ cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch&
                                const ColScratch& s_bg, int32_t* D_obj, int32_t* F_obj,
                                int32_t* D_bg, int32_t* F_bg, cudaStream_t stream, int band0 = 0,
                                int nbl = -1);
+// City-block row pass (Sec. 2.1): D from the column-pass scratch of the
+// chosen sources.
+cudaError_t launch_cityblock_rows(int H, int W, const ColGeom& g, const ColScratch& s, int32_t* D,
+                                  cudaStream_t stream);
 cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
                            const ColScratch& s, uint32_t* P, cudaStream_t stream);
 cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,

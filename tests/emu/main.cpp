@@ -9,6 +9,7 @@
 extern "C" {
 int oracle_edt2d(const uint8_t* mask, int M, int L, int mode, int32_t* D, int32_t* F);
 int oracle_edt3d(const uint8_t* mask, int Z, int M, int L, int mode, int32_t* D, int32_t* F);
+int oracle_cityblock2d(const uint8_t* mask, int M, int L, int mode, int stop, int32_t* D);
 }
 using namespace edt;
 
@@ -110,8 +111,45 @@ static int run3d(int Dz, int H, int W, double p, int mode)
     return bad;
 }
 
+static int run_cityblock(int H, int W, double p, int mode, int align_off)
+{
+    std::vector<uint8_t> mask((size_t)H * W);
+    for (auto& m : mask) m = urand() < p;
+    const ColGeom g = col_geom(H, W);
+    std::vector<unsigned char> sa(col_scratch_bytes(g) + 256);
+    ColScratch s = col_scratch_carve((void*)(((uintptr_t)sa.data() + 255) & ~uintptr_t(255)), g);
+    memset(s.cnt, 0, g.ntiles * 4);
+    const size_t n = (size_t)H * W;
+    int32_t* Db = alloc_words(n + align_off);
+    int32_t* D = Db + align_off;
+    launch_colbits(mask.data(), g, mode, s, nullptr);
+    launch_cityblock_rows(H, W, g, s, D, nullptr);
+    std::vector<int32_t> Do(n);
+    oracle_cityblock2d(mask.data(), H, W, mode, 0, Do.data());
+    int bad = 0;
+    for (size_t i = 0; i < n && bad < 5; ++i)
+        if (D[i] != Do[i]) { fprintf(stderr, "city-block mismatch %dx%d mode %d at %zu: %d vs %d\n", H, W, mode, i, D[i], Do[i]); ++bad; }
+    free(Db);
+    return bad;
+}
+
 int main(int argc, char** argv)
 {
+    if (argc > 1 && !strcmp(argv[1], "cityblock")) {
+        const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
+        int bad = 0, cases = 0, run = 0;
+        const int shapes[][2] = {{1, 1}, {1, 9}, {9, 1}, {5, 7}, {33, 31}, {64, 100}, {40, 513}, {3, 2048},
+                                 {2, 8192}, {9, 8200}, {2, 16384}};
+        for (auto& sh : shapes)
+            for (double p : {0.0, 0.003, 0.05, 1.0}) {
+                const int c = cases++;
+                if (c % nparts != part) { for (long long i = 0; i < (long long)sh[0] * sh[1]; ++i) urand(); continue; }
+                ++run;
+                bad += run_cityblock(sh[0], sh[1], p, c & 1, c % 3 == 0 ? 4 : 0);
+            }
+        printf("cityblock cases %d bad %d\n", run, bad);
+        return bad != 0;
+    }
     if (argc > 1 && !strcmp(argv[1], "3d")) {
         int bad = 0, cases = 0;
         const int shapes[][3] = {{1, 1, 1}, {3, 5, 7}, {1, 40, 50}, {40, 1, 50}, {40, 50, 1},

@@ -72,6 +72,18 @@ static uint32_t xchg(uint32_t v, int src, const void* tag)
 }
 unsigned __shfl_sync(unsigned, unsigned v, int src) { return xchg(v, src, __builtin_return_address(0)); }
 int __shfl_sync(unsigned, int v, int src) { return (int)xchg((uint32_t)v, src, __builtin_return_address(0)); }
+int __shfl_up_sync(unsigned, int v, unsigned d)
+{
+    const int lane = g_f[g_cur].tid & 31;
+    const int src = lane >= (int)d ? lane - (int)d : lane;
+    return (int)xchg((uint32_t)v, src, __builtin_return_address(0));
+}
+int __shfl_down_sync(unsigned, int v, unsigned d)
+{
+    const int lane = g_f[g_cur].tid & 31;
+    const int src = lane + (int)d < 32 ? lane + (int)d : lane;
+    return (int)xchg((uint32_t)v, src, __builtin_return_address(0));
+}
 static unsigned ballot_tag(int pred, const void* tag)
 {
     const int t = g_f[g_cur].tid;

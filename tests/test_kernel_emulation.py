@@ -1,5 +1,5 @@
 """The CUDA kernels of libedt (column pass, 2-D row pass alone and fused for
-both transforms, 3-D y and x passes) compiled as C++ and run on the CPU by a
+both transforms, 3-D y and x passes, city-block row pass) compiled as C++ and run on the CPU by a
 host emulation (tests/emu): one fiber per CUDA thread, barriers and warp
 collectives emulated, dynamic shared memory allocated at exactly the
 launch's size under AddressSanitizer.  The results must equal the oracle's
@@ -29,15 +29,18 @@ def _build():
     subprocess.run([sys.executable, os.path.join(EMU, "prepare.py"), os.path.join(BUILD, "src")], check=True)
     san = ["-fsanitize=address,undefined", "-fno-omit-frame-pointer", "-g", "-O1"]
     oracle_o = os.path.join(BUILD, "oracle.o")
+    nedt_o = os.path.join(BUILD, "nedt_oracle.o")
     subprocess.run([gcc, "-O1", "-c", os.path.join(ROOT, "oracle", "edt_oracle.c"), "-o", oracle_o] + san,
+                   check=True)
+    subprocess.run([gcc, "-O1", "-c", os.path.join(ROOT, "oracle", "nedt_oracle.c"), "-o", nedt_o] + san,
                    check=True)
     exe = os.path.join(BUILD, "emu")
     src = os.path.join(BUILD, "src")
     cmd = [gxx, "-std=c++20", "-Wno-unknown-pragmas", "-I", EMU, "-I", BUILD, "-I", os.path.join(ROOT, "include"),
            "-include", os.path.join(EMU, "shim.h")] + san + [
         "-x", "c++", os.path.join(src, "edt_colpass.cu"), "-x", "c++", os.path.join(src, "edt_rows2d.cu"),
-        "-x", "c++", os.path.join(src, "edt_3d.cu"), "-x", "none", os.path.join(EMU, "runtime.cpp"),
-        os.path.join(EMU, "main.cpp"), oracle_o, "-o", exe, "-lpthread"]
+        "-x", "c++", os.path.join(src, "edt_3d.cu"), "-x", "c++", os.path.join(src, "edt_cityblock.cu"), "-x", "none", os.path.join(EMU, "runtime.cpp"),
+        os.path.join(EMU, "main.cpp"), oracle_o, nedt_o, "-o", exe, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise AssertionError("emulation build failed:\n" + r.stderr[-4000:])
@@ -65,3 +68,8 @@ def test_kernels_2d_match_oracle(emu):
 
 def test_kernels_3d_match_oracle(emu):
     _run_all([[emu, "3d"]])
+
+
+def test_cityblock_kernel_matches_oracle(emu):
+    n = max(1, min(8, os.cpu_count() or 1))
+    _run_all([[emu, "cityblock", str(k), str(n)] for k in range(n)])

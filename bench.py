@@ -250,17 +250,19 @@ def measure_volume(edt, torch, dev, reps=10):
             "effective_gbs_9B_per_vox": 9 * n / (ms / 1e3) / 1e9, "kernel_ms": kern}
 
 
-def measure_cityblock(edt, torch, dev, mask_np, reps=20):
-    """City-block transform (Sec. 2.1) of the same 8192^2 discs mask, both
-    source classes per step: CUDA events per step with the 256 MiB L2 flush
-    in between (untimed), kernel times from libedt's tracing."""
+def measure_nedt(edt, torch, dev, mask_np, kind, reps=20):
+    """City-block (Sec. 2.1) or chamfer 4-3 (Sec. 2.2) transform of the same
+    8192^2 discs mask, both source classes per step: CUDA events per step with
+    the 256 MiB L2 flush in between (untimed), kernel times from libedt's
+    tracing."""
+    fn = edt.cityblock if kind == "cityblock" else edt.chamfer43
     m = torch.from_numpy(mask_np).to(dev)
     D = [torch.empty(m.shape, dtype=torch.int32, device=dev) for _ in range(2)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(3):
         for mode in (0, 1):
-            edt.cityblock(m, mode, out=D[mode])
+            fn(m, mode, out=D[mode])
     torch.cuda.synchronize()
     edt.trace_enable(True)
     total = 0.0
@@ -270,15 +272,16 @@ def measure_cityblock(edt, torch, dev, mask_np, reps=20):
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for mode in (0, 1):
-            edt.cityblock(m, mode, out=D[mode])
+            fn(m, mode, out=D[mode])
         b.record(stream)
         torch.cuda.synchronize()
         total += a.elapsed_time(b)
-    k_ms = {k: edt.trace_read(k)[0] / (2 * reps) for k in ("k_colbits", "k_cityblock_rows")}
+    names = ("k_colbits", "k_cityblock_rows") if kind == "cityblock" else ("k_chamfer",)
+    k_ms = {k: edt.trace_read(k)[0] / (2 * reps) for k in names}
     edt.trace_enable(False)
     ms = total / reps
     px = 2 * m.numel()
-    return {"workload": "city-block DT of the 8192x8192 discs mask, to object and to background per step, int32 D",
+    return {"workload": f"{kind} DT of the 8192x8192 discs mask, to object and to background per step, int32 D",
             "ms_per_step": ms, "gpx_s": px / (ms / 1e3) / 1e9,
             "effective_gbs_5B_per_px": 5 * px / (ms / 1e3) / 1e9, "kernel_ms_per_transform": k_ms}
 
@@ -485,9 +488,13 @@ def run_gpu(args, rank, world, local_rank):
         except Exception as exc:
             extras["volume"] = {"error": repr(exc)}
         try:
-            extras["cityblock"] = measure_cityblock(edt, torch, dev, mask_np)
+            extras["cityblock"] = measure_nedt(edt, torch, dev, mask_np, "cityblock")
         except Exception as exc:  # noqa: BLE001
             extras["cityblock"] = {"error": repr(exc)}
+        try:
+            extras["chamfer43"] = measure_nedt(edt, torch, dev, mask_np, "chamfer")
+        except Exception as exc:  # noqa: BLE001
+            extras["chamfer43"] = {"error": repr(exc)}
         try:
             extras["serve"] = measure_serve(edt, torch)
         except Exception as exc:

@@ -121,6 +121,17 @@ edt_status edt_feature_pair_host(const uint8_t *mask, int ndim, const int *shape
 edt_status edt_cityblock2d(const uint8_t *mask, int H, int W, int mode,
                            int32_t *D, edt_stream_t stream);
 
+/* Chamfer 4-3 distance transform of a 2-D image (Sec. 2.2): D[i][j] = the
+ * smallest 3 max(|i - a|, |j - b|) + min(|i - a|, |j - b|) over the source
+ * pixels (a, b) of `mode` -- the cost of the cheapest path with steps of 3
+ * (horizontal, vertical) and 4 (diagonal), the result of the paper's two
+ * raster scans -- INT32_MAX when the image has no source.  Device pointers;
+ * D is H x W int32, row-major; scratch (about 4.5 bytes per pixel plus
+ * 2 bytes per pixel and row of sheared images) comes from the stream-ordered
+ * pool.  Errors as edt_sq2d. */
+edt_status edt_chamfer43_2d(const uint8_t *mask, int H, int W, int mode,
+                            int32_t *D, edt_stream_t stream);
+
 /* One transform in a batch.  Pointers are device memory; F required, D and
  * dist may be NULL; shape[2] is ignored for ndim = 2. */
 typedef struct {

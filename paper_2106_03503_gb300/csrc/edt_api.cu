@@ -441,6 +441,27 @@ edt_status edt_cityblock2d(const uint8_t* mask, int H, int W, int mode, int32_t*
     return st;
 }
 
+edt_status edt_chamfer43_2d(const uint8_t* mask, int H, int W, int mode, int32_t* D, edt_stream_t stream_)
+{
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int shape[2] = {H, W};
+    edt_status st = check_shape(2, shape, mode);
+    if (st != EDT_OK) return st;
+    if (!mask || !D) return fail(EDT_ERR_INVALID, "mask and D must not be NULL");
+    int sms = 0;
+    if ((st = device_setup(&sms)) != EDT_OK) return st;
+    void* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, chamfer_scratch_bytes(H, W), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (scratch)");
+    if ((e = traced("k_chamfer", stream, [&] { return launch_chamfer(mask, H, W, mode, D, scratch, sms, stream); })) !=
+        cudaSuccess)
+        st = cuda_fail(e, "chamfer launches");
+    e = cudaFreeAsync(scratch, stream);
+    if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync");
+    if (st == EDT_OK) clear_error();
+    return st;
+}
+
 edt_status edt_feature_host(const uint8_t* mask, int ndim, const int* shape,
                             int mode, int32_t* D, int32_t* F, float* dist,
                             edt_stream_t stream)

@@ -56,6 +56,10 @@ cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch&
 // chosen sources.
 cudaError_t launch_cityblock_rows(int H, int W, const ColGeom& g, const ColScratch& s, int32_t* D,
                                   cudaStream_t stream);
+// Chamfer 4-3 transform (Sec. 2.2): scratch size and the whole pass sequence.
+size_t chamfer_scratch_bytes(int H, int W);
+cudaError_t launch_chamfer(const uint8_t* mask, int H, int W, int mode, int32_t* D, void* scratch,
+                           int sm_count, cudaStream_t stream);
 cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
                            const ColScratch& s, uint32_t* P, cudaStream_t stream);
 cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,

@@ -58,6 +58,7 @@ _lib.edt_feature_host.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp, _
 _lib.edt_feature_pair.argtypes = [_vp, ctypes.c_int, _i32p, _vp, _vp, _vp, _vp, _vp]
 _lib.edt_feature_pair_host.argtypes = [_vp, ctypes.c_int, _i32p, _vp, _vp, _vp, _vp, _vp]
 _lib.edt_cityblock2d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
+_lib.edt_chamfer43_2d.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
 _lib.edt_trace_enable.argtypes = [ctypes.c_int]
 _lib.edt_trace_enable.restype = ctypes.c_int
 _lib.edt_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -69,7 +70,8 @@ for _name in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host", "edt_fe
     getattr(_lib, _name).restype = ctypes.c_int
 
 EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_pair", "edt_feature_host",
-           "edt_feature_pair_host", "edt_cityblock2d", "edt_plan_create",
+           "edt_feature_pair_host", "edt_cityblock2d", "edt_chamfer43_2d",
+           "edt_plan_create",
            "edt_plan_destroy", "edt_batch", "edt_serve_create", "edt_serve_submit",
            "edt_serve_poll", "edt_serve_destroy", "edt_trace_enable", "edt_trace_read",
            "edt_last_error", "edt_version")
@@ -296,6 +298,18 @@ def cityblock(mask, mode: int = TO_OBJECT, out=None, stream=None):
         raise ValueError("the city-block transform takes 2-D images")
     D = out if out is not None else torch.empty(m.shape, dtype=torch.int32, device=m.device)
     _check(_lib.edt_cityblock2d(_ptr(m), m.shape[0], m.shape[1], int(mode), _ptr(D), _stream_handle(stream)))
+    return D
+
+
+def chamfer43(mask, mode: int = TO_OBJECT, out=None, stream=None):
+    """Chamfer 4-3 distance transform of a 2-D uint8 CUDA tensor (Sec. 2.2):
+    int32 distances (3 per straight step, 4 per diagonal step), INT32_MAX
+    without a source."""
+    m = _mask_arg(mask)
+    if m.dim() != 2:
+        raise ValueError("the chamfer transform takes 2-D images")
+    D = out if out is not None else torch.empty(m.shape, dtype=torch.int32, device=m.device)
+    _check(_lib.edt_chamfer43_2d(_ptr(m), m.shape[0], m.shape[1], int(mode), _ptr(D), _stream_handle(stream)))
     return D
 
 

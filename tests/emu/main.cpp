@@ -10,6 +10,7 @@ extern "C" {
 int oracle_edt2d(const uint8_t* mask, int M, int L, int mode, int32_t* D, int32_t* F);
 int oracle_edt3d(const uint8_t* mask, int Z, int M, int L, int mode, int32_t* D, int32_t* F);
 int oracle_cityblock2d(const uint8_t* mask, int M, int L, int mode, int stop, int32_t* D);
+int oracle_chamfer43_2d(const uint8_t* mask, int M, int L, int mode, int stop, int32_t* D);
 }
 using namespace edt;
 
@@ -133,8 +134,41 @@ static int run_cityblock(int H, int W, double p, int mode, int align_off)
     return bad;
 }
 
+static int run_chamfer(int H, int W, double p, int mode)
+{
+    std::vector<uint8_t> mask((size_t)H * W);
+    for (auto& m : mask) m = urand() < p;
+    std::vector<unsigned char> scratch(chamfer_scratch_bytes(H, W) + 256);
+    void* sbase = (void*)(((uintptr_t)scratch.data() + 255) & ~uintptr_t(255));
+    const size_t n = (size_t)H * W;
+    int32_t* D = alloc_words(n);
+    launch_chamfer(mask.data(), H, W, mode, D, sbase, 4, nullptr);
+    std::vector<int32_t> Do(n);
+    oracle_chamfer43_2d(mask.data(), H, W, mode, 0, Do.data());
+    int bad = 0;
+    for (size_t i = 0; i < n && bad < 5; ++i)
+        if (D[i] != Do[i]) { fprintf(stderr, "chamfer mismatch %dx%d mode %d at %zu: %d vs %d\n", H, W, mode, i, D[i], Do[i]); ++bad; }
+    free(D);
+    return bad;
+}
+
 int main(int argc, char** argv)
 {
+    if (argc > 1 && !strcmp(argv[1], "chamfer")) {
+        const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
+        int bad = 0, cases = 0, run = 0;
+        const int shapes[][2] = {{1, 1}, {1, 9}, {9, 1}, {5, 7}, {33, 31}, {64, 100}, {130, 70}, {40, 513},
+                                 {3, 2048}, {2, 8200}, {300, 40}};
+        for (auto& sh : shapes)
+            for (double p : {0.0, 0.003, 0.05, 1.0}) {
+                const int c = cases++;
+                if (c % nparts != part) { for (long long i = 0; i < (long long)sh[0] * sh[1]; ++i) urand(); continue; }
+                ++run;
+                bad += run_chamfer(sh[0], sh[1], p, c & 1);
+            }
+        printf("chamfer cases %d bad %d\n", run, bad);
+        return bad != 0;
+    }
     if (argc > 1 && !strcmp(argv[1], "cityblock")) {
         const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
         int bad = 0, cases = 0, run = 0;

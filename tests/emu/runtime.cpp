@@ -31,12 +31,27 @@ static int g_cur = -1;
 static unsigned char* g_smem = nullptr;
 static size_t g_smem_bytes = 0;
 static std::function<void()> g_body;
-static unsigned g_block, g_blocks, g_threads;
+static unsigned g_block, g_blocks, g_threads, g_gridx = 0;
 static uint32_t g_slot[32][32];   // [warp][lane]
 thread_local EmuDim threadIdx, blockIdx, blockDim, gridDim;
 static const void* g_main_stack_bottom; static size_t g_main_stack_size;
 
-static void set_ids(int t) { threadIdx.x = t; blockIdx.x = g_block; blockDim.x = g_threads; gridDim.x = g_blocks; }
+static void set_ids(int t)
+{
+    threadIdx.x = t;
+    blockDim.x = g_threads;
+    if (g_gridx) {
+        blockIdx.x = g_block % g_gridx;
+        blockIdx.y = g_block / g_gridx;
+        gridDim.x = g_gridx;
+        gridDim.y = g_blocks / g_gridx;
+    } else {
+        blockIdx.x = g_block;
+        blockIdx.y = 0;
+        gridDim.x = g_blocks;
+        gridDim.y = 1;
+    }
+}
 
 static void yield_to_main()
 {
@@ -109,7 +124,19 @@ unsigned __reduce_and_sync(unsigned, unsigned v)
 unsigned char* emu_smem() { return g_smem; }
 size_t emu_smem_bytes() { return g_smem_bytes; }
 
+static void launch_blocks(unsigned blocks, unsigned threads, size_t smem, std::function<void()> body);
 void emu_launch(unsigned blocks, unsigned threads, size_t smem, std::function<void()> body)
+{
+    g_gridx = 0;
+    launch_blocks(blocks, threads, smem, body);
+}
+void emu_launch(const dim3& grid, unsigned threads, size_t smem, std::function<void()> body)
+{
+    g_gridx = grid.x;
+    launch_blocks(grid.x * grid.y, threads, smem, body);
+    g_gridx = 0;
+}
+static void launch_blocks(unsigned blocks, unsigned threads, size_t smem, std::function<void()> body)
 {
     if (threads % 32 != 0 || threads == 0 || threads > 1024) { fprintf(stderr, "bad block size %u\n", threads); abort(); }
     if (smem > 227 * 1024) { fprintf(stderr, "smem %zu too large\n", smem); abort(); }

@@ -31,6 +31,7 @@ template <class A, class B> inline typename std::common_type<A, B>::type min(A a
 template <class A, class B> inline typename std::common_type<A, B>::type max(A a, B b) { return a > b ? a : b; }
 
 struct EmuDim { unsigned x = 0, y = 0, z = 0; };
+struct dim3 { unsigned x = 1, y = 1, z = 1; dim3(unsigned a = 1, unsigned b = 1, unsigned c = 1) : x(a), y(b), z(c) {} };
 extern thread_local EmuDim threadIdx, blockIdx, blockDim, gridDim;
 
 struct int4 { int x, y, z, w; };
@@ -72,12 +73,15 @@ int __any_sync(unsigned mask, int pred);
 unsigned char* emu_smem();
 size_t emu_smem_bytes();
 void emu_launch(unsigned blocks, unsigned threads, size_t smem, std::function<void()> body);
+void emu_launch(const dim3& grid, unsigned threads, size_t smem, std::function<void()> body);
 
 // CUDA runtime / driver stand-ins
 typedef int cudaError_t;
 constexpr int cudaSuccess = 0;
 typedef void* cudaStream_t;
 inline cudaError_t cudaGetLastError() { return 0; }
+inline cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t) { memset(p, v, n); return 0; }
+
 enum cudaFuncAttribute { cudaFuncAttributeMaxDynamicSharedMemorySize };
 template <class F> inline cudaError_t cudaFuncSetAttribute(F, cudaFuncAttribute, int) { return 0; }
 template <class F> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int* n, F, int, size_t) { *n = 2; return 0; }

@@ -1,5 +1,5 @@
 """The CUDA kernels of libedt (column pass, 2-D row pass alone and fused for
-both transforms, 3-D y and x passes, city-block row pass) compiled as C++ and run on the CPU by a
+both transforms, 3-D y and x passes, city-block row pass, chamfer 4-3 passes) compiled as C++ and run on the CPU by a
 host emulation (tests/emu): one fiber per CUDA thread, barriers and warp
 collectives emulated, dynamic shared memory allocated at exactly the
 launch's size under AddressSanitizer.  The results must equal the oracle's
@@ -39,7 +39,8 @@ def _build():
     cmd = [gxx, "-std=c++20", "-Wno-unknown-pragmas", "-I", EMU, "-I", BUILD, "-I", os.path.join(ROOT, "include"),
            "-include", os.path.join(EMU, "shim.h")] + san + [
         "-x", "c++", os.path.join(src, "edt_colpass.cu"), "-x", "c++", os.path.join(src, "edt_rows2d.cu"),
-        "-x", "c++", os.path.join(src, "edt_3d.cu"), "-x", "c++", os.path.join(src, "edt_cityblock.cu"), "-x", "none", os.path.join(EMU, "runtime.cpp"),
+        "-x", "c++", os.path.join(src, "edt_3d.cu"), "-x", "c++", os.path.join(src, "edt_cityblock.cu"),
+        "-x", "c++", os.path.join(src, "edt_chamfer.cu"), "-x", "none", os.path.join(EMU, "runtime.cpp"),
         os.path.join(EMU, "main.cpp"), oracle_o, nedt_o, "-o", exe, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -73,3 +74,8 @@ def test_kernels_3d_match_oracle(emu):
 def test_cityblock_kernel_matches_oracle(emu):
     n = max(1, min(8, os.cpu_count() or 1))
     _run_all([[emu, "cityblock", str(k), str(n)] for k in range(n)])
+
+
+def test_chamfer_kernels_match_oracle(emu):
+    n = max(1, min(8, os.cpu_count() or 1))
+    _run_all([[emu, "chamfer", str(k), str(n)] for k in range(n)])

@@ -276,7 +276,8 @@ def measure_nedt(edt, torch, dev, mask_np, kind, reps=20):
         b.record(stream)
         torch.cuda.synchronize()
         total += a.elapsed_time(b)
-    names = ("k_colbits", "k_cityblock_rows") if kind == "cityblock" else ("k_chamfer",)
+    names = (("k_colbits", "k_cityblock_rows") if kind == "cityblock" else
+             ("k_shear", "k_colbits", "k_chamfer_rows", "k_chamfer_cols"))
     k_ms = {k: edt.trace_read(k)[0] / (2 * reps) for k in names}
     edt.trace_enable(False)
     ms = total / reps

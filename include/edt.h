@@ -128,7 +128,9 @@ edt_status edt_cityblock2d(const uint8_t *mask, int H, int W, int mode,
  * raster scans -- INT32_MAX when the image has no source.  Device pointers;
  * D is H x W int32, row-major; scratch (about 4.5 bytes per pixel plus
  * 2 bytes per pixel and row of sheared images) comes from the stream-ordered
- * pool.  Errors as edt_sq2d. */
+ * pool.  Errors as edt_sq2d; rows wider than 14336 columns return
+ * EDT_ERR_TOO_LARGE (a block keeps two sheared column records of 8 bytes per
+ * column of its rows in shared memory). */
 edt_status edt_chamfer43_2d(const uint8_t *mask, int H, int W, int mode,
                             int32_t *D, edt_stream_t stream);
 

@@ -59,6 +59,7 @@ edt_status device_setup(int* sm_count)
             if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
             if ((e = set_2d_attributes()) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
             if ((e = set_3d_attributes()) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            if ((e = set_chamfer_attributes()) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
             // keep freed scratch in this process's default pool instead of
             // returning it to the driver at every synchronisation
             cudaMemPool_t pool = nullptr;
@@ -448,13 +449,13 @@ edt_status edt_chamfer43_2d(const uint8_t* mask, int H, int W, int mode, int32_t
     edt_status st = check_shape(2, shape, mode);
     if (st != EDT_OK) return st;
     if (!mask || !D) return fail(EDT_ERR_INVALID, "mask and D must not be NULL");
+    if (W > 14336) return fail(EDT_ERR_TOO_LARGE, "chamfer rows are limited to 14336 columns (got %d)", W);
     int sms = 0;
     if ((st = device_setup(&sms)) != EDT_OK) return st;
     void* scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, chamfer_scratch_bytes(H, W), stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (scratch)");
-    if ((e = traced("k_chamfer", stream, [&] { return launch_chamfer(mask, H, W, mode, D, scratch, sms, stream); })) !=
-        cudaSuccess)
+    if ((e = launch_chamfer(mask, H, W, mode, D, scratch, sms, stream)) != cudaSuccess)
         st = cuda_fail(e, "chamfer launches");
     e = cudaFreeAsync(scratch, stream);
     if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync");

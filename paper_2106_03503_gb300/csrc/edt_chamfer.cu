@@ -19,9 +19,9 @@
 //       column u of the second the anti-diagonal i + j = u;
 //   (2) the column-bit kernel of the Euclidean transform runs on each, giving
 //       the nearest source along every diagonal;
-//   (3) k_chamfer_rows computes E for 8 rows per block (threads = columns)
-//       and the row term as two prefix minima (as in the city-block pass,
-//       weight 3), writing the row term to D and E to a scratch image;
+//   (3) k_chamfer_rows stages the sheared columns of 16 rows in shared
+//       memory, computes E and the row term as two prefix minima (weight 3),
+//       and writes the row term to D and E to a scratch image;
 //   (4) k_chamfer_cols_totals and k_chamfer_cols take the column term over
 //       chunks of 128 rows (chunk minima first, then each chunk with the
 //       minima of the chunks above and below it) and lower D to it.
@@ -30,7 +30,7 @@
 
 namespace edt {
 
-constexpr int CH_ROWS = 8;            // rows per block of the row kernel
+constexpr int CH_ROWS = 16;           // rows per block of the row kernel
 constexpr int CH_BIG = 1 << 29;       // no source
 constexpr int CH_CHUNK = 128;         // rows per chunk of the column kernels
 
@@ -64,110 +64,127 @@ __global__ void k_shear(const uint8_t* __restrict__ mask, int H, int W, int SW, 
     }
 }
 
-// Steps from row i to the nearest source of column `col` of a sheared image,
-// from its column-pass scratch (CH_BIG when the column has none).
-__device__ __forceinline__ int diag_steps(const ColScratch& s, int64_t SW, int b, int r, int i, int col)
+// Steps from row i (bit r of its band's word) to the nearest source of a
+// staged sheared column {w, up | dn << 16}; CH_BIG when the column has none.
+__device__ __forceinline__ int staged_steps(uint2 c, int base, int r, int i)
 {
-    const uint32_t w = s.C[(int64_t)b * SW + col];
-    const uint32_t a_ = w & (FULL >> (31 - r)), b_ = w & (FULL << r);
-    int up, dn;
-    if (a_) {
-        up = b * 32 + 31 - __clz(a_);
-    } else {
-        uint32_t u = s.U[(int64_t)b * SW + col] & 0xFFFFu;
-        if (u == (uint32_t)NONE16) u = s.GAB[(int64_t)(b >> 5) * SW + col] & 0xFFFFu;
-        up = (u == (uint32_t)NONE16) ? -CH_BIG : (int)u;
-    }
-    if (b_) {
-        dn = b * 32 + __ffs(b_) - 1;
-    } else {
-        uint32_t u = s.U[(int64_t)b * SW + col] >> 16;
-        if (u == (uint32_t)NONE16) u = s.GAB[(int64_t)(b >> 5) * SW + col] >> 16;
-        dn = (u == (uint32_t)NONE16) ? CH_BIG : (int)u;
-    }
+    const uint32_t a_ = c.x & (FULL >> (31 - r)), b_ = c.x & (FULL << r);
+    const uint32_t uo = c.y & 0xFFFFu, dno = c.y >> 16;
+    const int up = a_ ? base + 31 - __clz(a_) : (uo == (uint32_t)NONE16 ? -CH_BIG : (int)uo);
+    const int dn = b_ ? base + __ffs(b_) - 1 : (dno == (uint32_t)NONE16 ? CH_BIG : (int)dno);
     const int d = min(i - up, dn - i);
     return d < 32768 ? d : CH_BIG;     // real distances stay below 32768 rows
 }
 
-__device__ __forceinline__ int warp_incl_min_up(int v, int lane)
+// Column data {w, up | dn << 16} of column col of a sheared image's band b.
+__device__ __forceinline__ uint2 sheared_column(const ColScratch& s, int64_t SW, int b, int64_t col)
 {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(FULL, v, o);
-        if (lane >= o) v = min(v, u);
+    const uint32_t w = s.C[(int64_t)b * SW + col];
+    const uint32_t u = s.U[(int64_t)b * SW + col];
+    uint32_t up = u & 0xFFFFu, dn = u >> 16;
+    if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
+        const uint32_t gab = s.GAB[(int64_t)(b >> 5) * SW + col];
+        if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
+        if (dn == (uint32_t)NONE16) dn = gab >> 16;
     }
-    return v;
-}
-__device__ __forceinline__ int warp_incl_min_down(int v, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_down_sync(FULL, v, o);
-        if (lane + o < 32) v = min(v, u);
-    }
-    return v;
+    return make_uint2(w, up | (dn << 16));
 }
 
-// (3) E and the row term for 8 rows of one band; CPT columns per thread.
-template <int CPT>
+// (3) E and the row term for CH_ROWS rows of one band.  The sheared columns
+// these rows touch (W + CH_ROWS - 1 per direction) are staged in shared
+// memory first.  Warp w holds columns [w * 32 SL, (w + 1) * 32 SL), lane l the
+// columns w * 32 SL + 32 c + l (c < SL), so that loads and stores are
+// coalesced; a row's prefix minima run slice by slice with warp shuffles,
+// then across warps through shared memory.
+template <int SL>
 __global__ void __launch_bounds__(1024)
 k_chamfer_rows(int H, int W, int SW, ColScratch sd, ColScratch sa, int32_t* __restrict__ D,
                int32_t* __restrict__ E)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sx[32], sy[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = blockDim.x >> 5;
-    const int b = blockIdx.x >> 2;
-    const int r0 = (blockIdx.x & 3) * CH_ROWS;
-    const int c0 = t * CPT;
-    for (int rr = 0; rr < CH_ROWS; ++rr) {
-        const int r = r0 + rr, i = b * 32 + r;
-        if (i >= H) break;                                // uniform over the block
-        int e[CPT], px[CPT], sy_[CPT];
+    const int nblk_band = 32 / CH_ROWS;
+    const int b = blockIdx.x / nblk_band;
+    const int base = b * 32;
+    const int i0 = base + (blockIdx.x % nblk_band) * CH_ROWS;
+    if (i0 >= H) return;                                  // whole block
+    const int i1 = min(i0 + CH_ROWS, H);
+    const int span = W + (i1 - 1 - i0);
+    uint2* sD = reinterpret_cast<uint2*>(smem);           // diagonal columns H - i1 + x
+    uint2* sA = sD + (W + CH_ROWS);                       // anti-diagonal columns i0 + x
+    const int vbase = H - i1, ubase = i0;
+    for (int x = t; x < span; x += blockDim.x) {
+        sD[x] = sheared_column(sd, SW, b, vbase + x);
+        sA[x] = sheared_column(sa, SW, b, ubase + x);
+    }
+    __syncthreads();
+    const int jw = warp * 32 * SL;
+    for (int i = i0; i < i1; ++i) {
+        const int r = i - base;
+        int e[SL], px[SL], sq[SL];
         int run = CH_BIG;
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const int j = c0 + c;
+        for (int c = 0; c < SL; ++c) {
+            const int j = jw + 32 * c + lane;
             int ev = CH_BIG;
             if (j < W) {
-                const int dd = diag_steps(sd, SW, b, r, i, j - i + H - 1);
-                const int da = diag_steps(sa, SW, b, r, i, i + j);
+                const int dd = staged_steps(sD[j - i + H - 1 - vbase], base, r, i);
+                const int da = staged_steps(sA[i + j - ubase], base, r, i);
                 const int dm = min(dd, da);
                 ev = dm >= CH_BIG ? CH_BIG : 4 * dm;
             }
             e[c] = ev;
-            run = min(run, ev - 3 * j);
-            px[c] = run;
-            sy_[c] = ev + 3 * j;
+            // slice prefix of E(k) - 3k, continued from the previous slices
+            int v = ev - 3 * j;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(FULL, v, o);
+                if (lane >= o) v = min(v, u);
+            }
+            v = min(v, run);
+            px[c] = v;
+            run = __shfl_sync(FULL, v, 31);
         }
         int suf = CH_BIG;
 #pragma unroll
-        for (int c = CPT - 1; c >= 0; --c) {
-            suf = min(suf, sy_[c]);
-            sy_[c] = suf;
+        for (int c = SL - 1; c >= 0; --c) {
+            const int j = jw + 32 * c + lane;
+            int v = e[c] + 3 * j;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_down_sync(FULL, v, o);
+                if (lane + o < 32) v = min(v, u);
+            }
+            v = min(v, suf);
+            sq[c] = v;
+            suf = __shfl_sync(FULL, v, 0);
         }
-        const int ix = warp_incl_min_up(run, lane), iy = warp_incl_min_down(suf, lane);
-        if (lane == 31) sx[warp] = ix;
-        if (lane == 0) sy[warp] = iy;
+        if (lane == 0) {
+            sx[warp] = run;
+            sy[warp] = suf;
+        }
         __syncthreads();
         if (warp == 0) {
-            const int vx = lane < nwarp ? sx[lane] : CH_BIG;
-            const int vy = lane < nwarp ? sy[lane] : CH_BIG;
-            const int ex = warp_incl_min_up(vx, lane), ey = warp_incl_min_down(vy, lane);
-            sx[lane] = ex;
-            sy[lane] = ey;
+            int vx = lane < nwarp ? sx[lane] : CH_BIG, vy = lane < nwarp ? sy[lane] : CH_BIG;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int ux = __shfl_up_sync(FULL, vx, o), uy = __shfl_down_sync(FULL, vy, o);
+                if (lane >= o) vx = min(vx, ux);
+                if (lane + o < 32) vy = min(vy, uy);
+            }
+            sx[lane] = vx;
+            sy[lane] = vy;
         }
         __syncthreads();
-        int carry_x = __shfl_up_sync(FULL, ix, 1), carry_y = __shfl_down_sync(FULL, iy, 1);
-        if (lane == 0) carry_x = CH_BIG;
-        if (lane == 31) carry_y = CH_BIG;
-        if (warp > 0) carry_x = min(carry_x, sx[warp - 1]);
-        if (warp + 1 < nwarp) carry_y = min(carry_y, sy[warp + 1]);
+        const int cx = warp > 0 ? sx[warp - 1] : CH_BIG;
+        const int cy = warp + 1 < nwarp ? sy[warp + 1] : CH_BIG;
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const int j = c0 + c;
+        for (int c = 0; c < SL; ++c) {
+            const int j = jw + 32 * c + lane;
             if (j < W) {
                 const int64_t o = (int64_t)i * W + j;
-                D[o] = min(3 * j + min(carry_x, px[c]), -3 * j + min(carry_y, sy_[c]));
+                D[o] = min(3 * j + min(cx, px[c]), -3 * j + min(cy, sq[c]));
                 E[o] = e[c];
             }
         }
@@ -195,7 +212,9 @@ __global__ void k_chamfer_cols_totals(int H, int W, const int32_t* __restrict__ 
 
 // (4b) the column term of every pixel of a chunk, with the other chunks'
 // minima as carries; D becomes min(row term, column term), INT32_MAX where
-// no source exists.
+// no source exists.  (Keeping the term from below in shared memory instead
+// of a second pass over D was slower: 64 KB per 128 columns left too few
+// warps per SM for these sequential loops.)
 __global__ void k_chamfer_cols(int H, int W, const int32_t* __restrict__ E, const int* __restrict__ Tf,
                                const int* __restrict__ Tb, int nq, int32_t* __restrict__ D)
 {
@@ -252,21 +271,44 @@ cudaError_t launch_chamfer(const uint8_t* mask, int H, int W, int mode, int32_t*
     cudaError_t e;
     if ((e = cudaMemsetAsync(sd.cnt, 0, (size_t)gs.ntiles * 4, stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(sa.cnt, 0, (size_t)gs.ntiles * 4, stream)) != cudaSuccess) return e;
-    k_shear<<<sm_count * 8, 256, 0, stream>>>(mask, H, W, SW, mode, Sd, Sa);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_colbits(Sd, gs, 0, sd, stream)) != cudaSuccess) return e;
-    if ((e = launch_colbits(Sa, gs, 0, sa, stream)) != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)(((H + 31) / 32) * 4);
-    if (W <= 8 * 1024)
-        k_chamfer_rows<8><<<blocks, ((W + 7) / 8 + 31) & ~31, 0, stream>>>(H, W, SW, sd, sa, D, E);
-    else
-        k_chamfer_rows<16><<<blocks, ((W + 15) / 16 + 31) & ~31, 0, stream>>>(H, W, SW, sd, sa, D, E);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = traced("k_shear", stream, [&] {
+             k_shear<<<sm_count * 8, 256, 0, stream>>>(mask, H, W, SW, mode, Sd, Sa);
+             return cudaGetLastError();
+         })) != cudaSuccess)
+        return e;
+    if ((e = traced("k_colbits", stream, [&] { return launch_colbits(Sd, gs, 0, sd, stream); })) != cudaSuccess)
+        return e;
+    if ((e = traced("k_colbits", stream, [&] { return launch_colbits(Sa, gs, 0, sa, stream); })) != cudaSuccess)
+        return e;
+    const unsigned blocks = (unsigned)(((H + 31) / 32) * (32 / CH_ROWS));
+    const size_t smem = 2 * (size_t)(W + CH_ROWS) * sizeof(uint2);
+    if ((e = traced("k_chamfer_rows", stream, [&] {
+             if (W <= 8 * 1024)
+                 k_chamfer_rows<8><<<blocks, ((W + 255) / 256) * 32, smem, stream>>>(H, W, SW, sd, sa, D, E);
+             else
+                 k_chamfer_rows<16><<<blocks, ((W + 511) / 512) * 32, smem, stream>>>(H, W, SW, sd, sa, D, E);
+             return cudaGetLastError();
+         })) != cudaSuccess)
+        return e;
     const dim3 grid((unsigned)((W + 127) / 128), (unsigned)nq);
-    k_chamfer_cols_totals<<<grid, 128, 0, stream>>>(H, W, E, Tf, Tb);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_chamfer_cols<<<grid, 128, 0, stream>>>(H, W, E, Tf, Tb, nq, D);
-    return cudaGetLastError();
+    return traced("k_chamfer_cols", stream, [&] {
+        k_chamfer_cols_totals<<<grid, 128, 0, stream>>>(H, W, E, Tf, Tb);
+        k_chamfer_cols<<<grid, 128, 0, stream>>>(H, W, E, Tf, Tb, nq, D);
+        return cudaGetLastError();
+    });
 }
 
+}  // namespace edt
+
+namespace edt {
+// The row kernel's dynamic shared memory: 2 x (W + CH_ROWS) x 8 bytes, at most
+// 229,632 bytes for the widest row accepted (14336); its static shared memory
+// (two 32-int arrays) has to fit beside it in the 227 KB of a block.
+cudaError_t set_chamfer_attributes()
+{
+    const int bytes = 226 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_chamfer_rows<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_chamfer_rows<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 }  // namespace edt

@@ -122,6 +122,7 @@ cudaError_t traced(const char* kernel, cudaStream_t stream, F&& launch)
 }
 
 cudaError_t set_2d_attributes();
+cudaError_t set_chamfer_attributes();
 cudaError_t set_3d_attributes();
 
 }  // namespace edt

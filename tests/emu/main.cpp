@@ -158,7 +158,7 @@ int main(int argc, char** argv)
         const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
         int bad = 0, cases = 0, run = 0;
         const int shapes[][2] = {{1, 1}, {1, 9}, {9, 1}, {5, 7}, {33, 31}, {64, 100}, {130, 70}, {40, 513},
-                                 {3, 2048}, {2, 8200}, {300, 40}};
+                                 {3, 2048}, {2, 8200}, {300, 40}, {17, 14336}};
         for (auto& sh : shapes)
             for (double p : {0.0, 0.003, 0.05, 1.0}) {
                 const int c = cases++;

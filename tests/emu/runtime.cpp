@@ -247,3 +247,11 @@ cudaError_t cudaGetDriverEntryPointByVersion(const char*, void** p, int, int, cu
     *q = 0;
     return 0;
 }
+
+// libedt's kernel tracing lives in its API file, which the emulation does
+// not build: tracing is off here.
+namespace edt {
+bool trace_on() { return false; }
+int trace_begin(const char*, cudaStream_t) { return 0; }
+void trace_end(int, cudaStream_t) {}
+}  // namespace edt

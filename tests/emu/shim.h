@@ -36,6 +36,8 @@ extern thread_local EmuDim threadIdx, blockIdx, blockDim, gridDim;
 
 struct int4 { int x, y, z, w; };
 struct uint4 { unsigned x, y, z, w; };
+struct uint2 { unsigned x, y; };
+inline uint2 make_uint2(unsigned a, unsigned b) { return {a, b}; }
 struct float4 { float x, y, z, w; };
 inline int4 make_int4(int a, int b, int c, int d) { return {a, b, c, d}; }
 inline float4 make_float4(float a, float b, float c, float d) { return {a, b, c, d}; }

@@ -63,7 +63,7 @@ def test_chamfer_paper_example_fig15():
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 37), (37, 1), (31, 33), (100, 64), (257, 1000), (300, 130),
-                                   (65, 2052), (40, 8192), (33, 8200), (9, 16384)])
+                                   (65, 2052), (40, 8192), (33, 8200), (9, 14336)])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_chamfer_random_masks(shape, mode):
     for k, p in enumerate([0.0, 0.001, 0.05, 0.5, 1.0]):
@@ -75,3 +75,11 @@ def test_chamfer_random_masks(shape, mode):
 def test_chamfer_full_size_discs(mode):
     m = inputs.discs_8192()
     np.testing.assert_array_equal(_gpu(m, mode, "chamfer"), oracle.chamfer43(m, mode))
+
+
+def test_chamfer_width_limit():
+    import torch
+    from paper_2106_03503_gb300 import edt
+    with pytest.raises(edt.EdtError) as e:
+        edt.chamfer43(torch.zeros((2, 14337), dtype=torch.uint8, device="cuda"))
+    assert e.value.status == 2

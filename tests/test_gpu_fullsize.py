@@ -25,3 +25,30 @@ def test_discs_8192_both_modes(mode):
 def test_blobs_512cube():
     m = inputs.blobs_512cube()
     check_against_oracle(m, 0, want_dist=False)
+
+
+def test_discs_8192_pair_as_benchmarked():
+    """The benchmark's step: edt_feature_pair on the 8192^2 discs mask (one
+    column pass and one row launch for both transforms); D equal to the
+    oracle on every pixel of both transforms, F a nearest source."""
+    import torch
+    from gpu_check import feature_valid_fast
+    from paper_2106_03503_gb300 import edt
+    m_np = inputs.discs_8192()
+    (Do, Fo), (Db, Fb) = edt.feature_pair(torch.from_numpy(m_np).cuda())
+    torch.cuda.synchronize()
+    for mode, (D, F) in ((0, (Do, Fo)), (1, (Db, Fb))):
+        D, F = D.cpu().numpy(), F.cpu().numpy()
+        np.testing.assert_array_equal(D, oracle.edt(m_np, mode)[0])
+        assert feature_valid_fast(m_np, mode, D, F) is None
+
+
+def test_discs_8192_pair_host_as_benchmarked():
+    """bench.py's e2e call (host buffers, row pass in four band ranges with
+    overlapped copies) on the full 8192^2 workload, against the oracle."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    m_np = inputs.discs_8192()
+    (Do, Fo), (Db, Fb) = edt.feature_pair_host(torch.from_numpy(m_np).pin_memory())
+    np.testing.assert_array_equal(Do.numpy(), oracle.edt(m_np, 0)[0])
+    np.testing.assert_array_equal(Db.numpy(), oracle.edt(m_np, 1)[0])

@@ -287,12 +287,16 @@ def measure_nedt(edt, torch, dev, mask_np, kind, reps=20):
             "effective_gbs_5B_per_px": 5 * px / (ms / 1e3) / 1e9, "kernel_ms_per_transform": k_ms}
 
 
-def measure_serve(edt, torch, n_jobs=600, warm=60, load=0.8, seed=5):
+def measure_serve(edt, torch, n_jobs=600, warm=200, loads=(0.5, 0.8), seed=5):
     """Serving: Poisson arrivals of mixed jobs (80 % 2-D squares of side
     128..4096 with Bernoulli density log-uniform 0.001..0.1, 20 % 3-D cubes of
     side 64..256 of smoothed noise), D+F, host buffers, 40 GB budget.  Masks
     are drawn from a pool of pre-generated masks of that recipe.  Capacity is
-    measured with a burst first; the arrival rate is `load` x capacity."""
+    measured in pixels per second with a burst of `warm` jobs (after 30
+    untimed ones); each Poisson run's arrival rate is one of `loads` x that
+    capacity divided by the mean size of the jobs that follow, so that the
+    offered load does not depend on which jobs happened to be in the burst.
+    The top-level numbers are those of the last load."""
     import numpy as np
     from paper_2106_03503_gb300 import inputs
     rng = np.random.default_rng(seed)
@@ -324,39 +328,54 @@ def measure_serve(edt, torch, n_jobs=600, warm=60, load=0.8, seed=5):
                 lats.append((r[0], n))
 
     order = rng.integers(0, len(pool), size=n_jobs + warm)
+
+    def burst(ids):
+        lats_b = []
+        k = 0
+        t0 = time.perf_counter()
+        while k < len(ids) or busy:
+            if k < len(ids) and free:
+                submit(int(ids[k]))
+                k += 1
+            else:
+                reap(lats_b)
+        return time.perf_counter() - t0, sum(n for _, n in lats_b)
+
+    burst(rng.integers(0, len(pool), size=30))            # untimed: pools, plans, graphs
     # capacity: keep `depth` jobs in flight
-    lats = []
-    t0 = time.perf_counter()
-    i = 0
-    while i < warm or busy:
-        if i < warm and free:
-            submit(int(order[i]))
-            i += 1
-        else:
+    secs, px_burst = burst(order[:warm])
+    cap_px = px_burst / secs
+    cap = warm / secs
+    # Poisson runs at load x capacity (in pixels), for each load
+    mean_px = float(np.mean([pool[int(k)].numel() for k in order[warm:]]))
+    runs = []
+    for ld in loads:
+        rate = ld * cap_px / mean_px
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
+        lats = []
+        start = time.perf_counter()
+        j = 0
+        while j < n_jobs or busy:
+            now = time.perf_counter() - start
+            if j < n_jobs and arrivals[j] <= now and free:
+                submit(int(order[warm + j]))
+                j += 1
+                continue
             reap(lats)
-    cap = warm / (time.perf_counter() - t0)
-    # Poisson run at load x capacity
-    rate = load * cap
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
-    lats = []
-    start = time.perf_counter()
-    j = 0
-    while j < n_jobs or busy:
-        now = time.perf_counter() - start
-        if j < n_jobs and arrivals[j] <= now and free:
-            submit(int(order[warm + j]))
-            j += 1
-            continue
-        reap(lats)
-    wall = time.perf_counter() - start
+        wall = time.perf_counter() - start
+        ms = sorted(1e3 * l for l, _ in lats)
+        px = sum(n for _, n in lats)
+        runs.append({"load": ld, "arrival_rate_jobs_s": rate, "jobs": len(lats),
+                     "throughput_gpx_s": px / wall / 1e9, "p50_ms": ms[len(ms) // 2],
+                     "p99_ms": ms[min(len(ms) - 1, int(round(0.99 * (len(ms) - 1))))]})
     srv.close()
-    ms = sorted(1e3 * l for l, _ in lats)
-    px = sum(n for _, n in lats)
+    main = runs[-1]
     return {"workload": "Poisson stream, 80% 2D side 128-4096 Bernoulli p log-uniform 0.001-0.1, "
                         "20% 3D side 64-256 smoothed noise; 40 GB budget, 3 streams, host buffers",
-            "jobs": len(lats), "arrival_rate_jobs_s": rate, "capacity_jobs_s": cap,
-            "throughput_gpx_s": px / wall / 1e9, "p50_ms": ms[len(ms) // 2],
-            "p99_ms": ms[min(len(ms) - 1, int(round(0.99 * (len(ms) - 1))))],
+            "capacity_jobs_s": cap, "capacity_gpx_s": cap_px / 1e9,
+            "load": main["load"], "jobs": main["jobs"], "arrival_rate_jobs_s": main["arrival_rate_jobs_s"],
+            "throughput_gpx_s": main["throughput_gpx_s"], "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "sweep": runs,
             "note": f"{len(pool)} pre-generated masks reused; at most {depth} jobs in flight"}
 
 

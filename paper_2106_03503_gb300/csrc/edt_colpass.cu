@@ -236,7 +236,9 @@ k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s, C
 }
 
 // Persistent column pass over every job of a batch: warp units are numbered
-// job by job (k1_first) and handed out in a grid-stride loop.
+// job by job (k1_first); every warp takes one contiguous range of them, so
+// that it finds its first job by binary search once and then steps from job
+// to job.
 __global__ void __launch_bounds__(K1_WARPS * 32)
 k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs)
 {
@@ -245,13 +247,18 @@ k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
     const int warp = threadIdx.x >> 5;
     const int64_t total = hdr->k1_total;
     const int nj = hdr->njobs;
-    for (int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp; gw < total;
-         gw += (int64_t)gridDim.x * K1_WARPS) {
-        int lo = 0, hi = nj - 1;
+    const int64_t nw = (int64_t)gridDim.x * K1_WARPS, w = (int64_t)blockIdx.x * K1_WARPS + warp;
+    const int64_t g0 = total * w / nw, g1 = total * (w + 1) / nw;
+    int lo = 0;
+    if (g0 < g1) {
+        int hi = nj - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].k1_first <= gw) lo = mid; else hi = mid - 1;
+            if (jobs[mid].k1_first <= g0) lo = mid; else hi = mid - 1;
         }
+    }
+    for (int64_t gw = g0; gw < g1; ++gw) {
+        while (lo + 1 < nj && jobs[lo + 1].k1_first <= gw) ++lo;
         const BatchJob& J = jobs[lo];
         const ColGeom g = J.g;
         const ColScratch s = J.s;

@@ -283,11 +283,14 @@ cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch&
 
 // --- batched row pass -------------------------------------------------------
 
-// Row-pass geometry of a batch job of width W: segments of 2^lg columns, NW
-// warps per band, `groups` bands side by side in one 16-warp block.
+// Row-pass geometry of a batch job of width W: segments of 2^lg columns (at
+// least 256: narrow images get fewer warps per band and more bands per block
+// instead of many short segments to merge), NW warps per band, `groups`
+// bands side by side in one 16-warp block.
 void batch_row_geometry(int W, int& lg, int& NW, int& groups)
 {
     lg = band_seg_log2(W, BATCH_K2_WARPS);
+    if (lg < 8) lg = 8;
     NW = (W + (1 << lg) - 1) >> lg;
     groups = BATCH_K2_WARPS / NW;
 }

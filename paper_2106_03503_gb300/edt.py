@@ -98,6 +98,14 @@ _lib.edt_batch.argtypes = [ctypes.c_void_p, ctypes.POINTER(Job), ctypes.c_int, _
 _lib.edt_batch.restype = ctypes.c_int
 
 
+# The same layout as Job (edt_job), for filling many jobs at once.
+_JOB_DTYPE = np.dtype({"names": ["mask", "ndim", "shape", "mode", "D", "F", "dist"],
+                       "formats": [np.uint64, np.int32, (np.int32, 3), np.int32, np.uint64, np.uint64, np.uint64],
+                       "offsets": [Job.mask.offset, Job.ndim.offset, Job.shape.offset, Job.mode.offset,
+                                   Job.D.offset, Job.F.offset, Job.dist.offset],
+                       "itemsize": ctypes.sizeof(Job)})
+
+
 def _job(mask, mode, D, F, dist):
     j = Job()
     j.mask = mask.data_ptr()
@@ -111,6 +119,24 @@ def _job(mask, mode, D, F, dist):
     return j
 
 
+class PreparedBatch:
+    """A filled job table (the layout of edt_job) plus references to the
+    tensors it points to."""
+
+    def __init__(self, jobs):
+        n = len(jobs)
+        arr = np.zeros(n, dtype=_JOB_DTYPE)
+        arr["mask"] = [j[0].data_ptr() for j in jobs]
+        arr["ndim"] = [j[0].dim() for j in jobs]
+        arr["shape"] = [tuple(j[0].shape) + (0,) * (3 - j[0].dim()) for j in jobs]
+        arr["mode"] = [int(j[1]) for j in jobs]
+        arr["D"] = [0 if j[2] is None else j[2].data_ptr() for j in jobs]
+        arr["F"] = [j[3].data_ptr() for j in jobs]
+        arr["dist"] = [0 if j[4] is None else j[4].data_ptr() for j in jobs]
+        self.arr = arr
+        self.jobs = list(jobs)
+
+
 class Plan:
     """A batch plan (edt_plan_create): runs up to n_max 2-D jobs of at most
     max_pixels pixels in total as one CUDA-graph replay."""
@@ -120,12 +146,21 @@ class Plan:
         _check(_lib.edt_plan_create(ctypes.byref(self._p), int(n_max), int(max_pixels)))
         self._keep = None
 
+    @staticmethod
+    def prepare(jobs):
+        """The job table of `jobs` ((mask, mode, D, F, dist) CUDA tensors; D,
+        dist may be None), for repeated runs of the same batch layout."""
+        return PreparedBatch(jobs)
+
     def run(self, jobs, stream=None):
         """jobs: sequence of (mask, mode, D, F, dist) CUDA tensors (D, dist may
-        be None).  Enqueues the batch on `stream`."""
-        arr = (Job * len(jobs))(*[_job(*j) for j in jobs])
-        self._keep = (arr, jobs)
-        _check(_lib.edt_batch(self._p, arr, len(jobs), _stream_handle(stream)))
+        be None), or a PreparedBatch.  Enqueues the batch on `stream`."""
+        if isinstance(jobs, PreparedBatch):
+            self._keep = jobs
+            _check(_lib.edt_batch(self._p, jobs.arr.ctypes.data_as(ctypes.POINTER(Job)), len(jobs.arr),
+                                  _stream_handle(stream)))
+            return
+        self.run(PreparedBatch(jobs), stream)
 
     def close(self):
         if self._p:

@@ -253,6 +253,46 @@ def measure_volume(edt, torch, dev, reps=10):
             "effective_gbs_9B_per_vox": 9 * n / (ms / 1e3) / 1e9, "kernel_ms": kern}
 
 
+def measure_small(edt, torch, dev, calls=2000):
+    """512 x 512 Bernoulli p = 0.01 image (seed 1), to object, D + F: one
+    plain edt_feature call after another on one stream, launch-latency bound.
+    Per call: GPU time by CUDA events around the call, and host wall time of
+    the call (the library's own enqueue work, before synchronising)."""
+    from paper_2106_03503_gb300 import inputs
+    m = torch.from_numpy(inputs.points_512()).to(dev)
+    D = torch.empty(m.shape, dtype=torch.int32, device=dev)
+    F = torch.empty_like(D)
+    stream = torch.cuda.current_stream()
+    for _ in range(50):
+        edt.feature(m, 0, out=(D, F, None))
+    torch.cuda.synchronize()
+    gpu, host = [], []
+    for _ in range(calls):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        t0 = time.perf_counter()
+        edt.feature(m, 0, out=(D, F, None))
+        host.append(1e6 * (time.perf_counter() - t0))
+        b.record(stream)
+        b.synchronize()
+        gpu.append(1e3 * a.elapsed_time(b))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        edt.feature(m, 0, out=(D, F, None))
+    torch.cuda.synchronize()
+    back_to_back = 1e6 * (time.perf_counter() - t0) / calls
+    gpu.sort()
+    host.sort()
+    q = lambda v, f: v[min(len(v) - 1, int(round(f * (len(v) - 1))))]  # noqa: E731
+    return {"workload": "2D 512x512 Bernoulli p=0.01 (seed 1), to object, D+F, plain edt_feature calls",
+            "calls": calls, "gpu_us_p50": q(gpu, 0.5), "gpu_us_p99": q(gpu, 0.99),
+            "host_enqueue_us_p50": q(host, 0.5), "host_enqueue_us_p99": q(host, 0.99),
+            "back_to_back_us_per_call": back_to_back,
+            "gpx_s_back_to_back": m.numel() / (back_to_back * 1e-6) / 1e9}
+
+
 def measure_nedt(edt, torch, dev, mask_np, kind, reps=20):
     """City-block (Sec. 2.1) or chamfer 4-3 (Sec. 2.2) transform of the same
     8192^2 discs mask, both source classes per step: CUDA events per step with
@@ -514,6 +554,10 @@ def run_gpu(args, rank, world, local_rank):
             extras["serve"] = {"error": repr(exc)}
         finally:
             gc.enable()
+        try:
+            extras["small"] = measure_small(edt, torch, dev)
+        except Exception as exc:  # noqa: BLE001
+            extras["small"] = {"error": repr(exc)}
         try:
             extras["batch"] = measure_batch(edt, torch, dev)
         except Exception as exc:  # report, do not hide

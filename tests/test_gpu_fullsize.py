@@ -52,3 +52,41 @@ def test_discs_8192_pair_host_as_benchmarked():
     (Do, Fo), (Db, Fb) = edt.feature_pair_host(torch.from_numpy(m_np).pin_memory())
     np.testing.assert_array_equal(Do.numpy(), oracle.edt(m_np, 0)[0])
     np.testing.assert_array_equal(Db.numpy(), oracle.edt(m_np, 1)[0])
+
+
+def _sparse_sources_check(shape, n_src, seed, mode):
+    """Largest accepted shapes: a few random sources (mode 0) or a few random
+    background pixels (mode 1); D and F checked on 20000 sampled pixels
+    against brute force over the sources (exact squared distances)."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(shape))
+    idx = rng.choice(n, size=n_src, replace=False)
+    flat = torch.zeros(n, dtype=torch.uint8, device="cuda") if mode == 0 else \
+        torch.ones(n, dtype=torch.uint8, device="cuda")
+    flat[torch.from_numpy(idx).cuda()] = 1 if mode == 0 else 0
+    D, F = edt.feature(flat.view(shape), mode)
+    torch.cuda.synchronize()
+    src = np.stack(np.unravel_index(idx, shape), -1).astype(np.int64)
+    sample = rng.choice(n, size=20000, replace=False)
+    p = np.stack(np.unravel_index(sample, shape), -1).astype(np.int64)
+    want = ((p[:, None, :] - src[None, :, :]) ** 2).sum(-1).min(1)
+    samp = torch.from_numpy(sample).cuda()
+    got_D = D.view(-1)[samp].cpu().numpy().astype(np.int64)
+    got_F = F.view(-1)[samp].cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(got_D, want)
+    assert np.all(np.isin(got_F, idx))
+    q = np.stack(np.unravel_index(got_F, shape), -1)
+    np.testing.assert_array_equal(((p - q) ** 2).sum(-1), want)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_largest_2d_image(mode):
+    """32767 x 16384 (537 M pixels, the largest side lengths accepted)."""
+    _sparse_sources_check((32767, 16384), 40, 5 + mode, mode)
+
+
+def test_largest_3d_lines():
+    """64 x 2048 x 1024: the largest y and x extents the 3-D passes accept."""
+    _sparse_sources_check((64, 2048, 1024), 30, 9, 0)

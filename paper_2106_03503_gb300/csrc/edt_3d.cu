@@ -93,7 +93,7 @@ k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
     const int z = blockIdx.x / xtiles;
     const int x0 = (blockIdx.x % xtiles) * 32;
     const int64_t plane = (int64_t)H * W;
-    const int zb = z >> 5, zr = z & 31, zG = zb >> 5;
+    const int zb = z >> 5, zr = z & 31, zG = zb >> s.gs;
 
     // nearest source along z of every (y, x) of the tile
     for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {

@@ -176,7 +176,7 @@ extern "C" edt_status edt_batch(edt_plan* p, const edt_job* jobs, int n, edt_str
         J.D = j.D;
         J.F = j.F;
         J.dist = j.dist;
-        J.g = col_geom(H, W);
+        J.g = col_geom(H, W, true);
         J.mode = j.mode;
         J.vec = (W % 16 == 0) && ((reinterpret_cast<uintptr_t>(j.mask) & 15) == 0);
         const size_t need = job_scratch_bytes(J.g);
@@ -189,6 +189,7 @@ extern "C" edt_status edt_batch(edt_plan* p, const edt_job* jobs, int n, edt_str
         J.s.GFL = reinterpret_cast<uint32_t*>(base + 2 * al256((size_t)J.g.nb * c));
         J.s.GAB = reinterpret_cast<uint32_t*>(base + 2 * al256((size_t)J.g.nb * c) + al256((size_t)J.g.nG * c));
         J.s.cnt = p->counters + cnt_off;
+        J.s.gs = J.g.gs;
         off += need;
         cnt_off += (size_t)J.g.ntiles;
         batch_row_geometry(W, J.lg, J.NW, J.groups);

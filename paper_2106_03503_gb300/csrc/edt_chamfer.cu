@@ -83,7 +83,7 @@ __device__ __forceinline__ uint2 sheared_column(const ColScratch& s, int64_t SW,
     const uint32_t u = s.U[(int64_t)b * SW + col];
     uint32_t up = u & 0xFFFFu, dn = u >> 16;
     if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
-        const uint32_t gab = s.GAB[(int64_t)(b >> 5) * SW + col];
+        const uint32_t gab = s.GAB[(int64_t)(b >> s.gs) * SW + col];
         if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
         if (dn == (uint32_t)NONE16) dn = gab >> 16;
     }

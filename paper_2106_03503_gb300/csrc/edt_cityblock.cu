@@ -64,7 +64,7 @@ k_cityblock_rows(int H, int W, ColScratch s, int32_t* __restrict__ D, int vec)
             const uint32_t u = s.U[(int64_t)b * W + col];
             uint32_t up = u & 0xFFFFu, dn = u >> 16;
             if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
-                const uint32_t gab = s.GAB[(int64_t)(b >> 5) * W + col];
+                const uint32_t gab = s.GAB[(int64_t)(b >> s.gs) * W + col];
                 if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
                 if (dn == (uint32_t)NONE16) dn = gab >> 16;
             }

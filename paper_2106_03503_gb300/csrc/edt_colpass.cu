@@ -11,7 +11,9 @@
 //     loads 32 consecutive bytes of its own row; ballot t transposes byte t of
 //     all 32 rows into the word of column t);
 //   - per band, the nearest source row above and below it inside its group of
-//     32 bands, from a forward and a backward scan over the group's words;
+//     bands (the smallest power of two, at most 32, that leaves a column at
+//     most 32 groups, so that small images still give many warps), from a
+//     forward and a backward scan over the group's words;
 //   - per group, the nearest source above and below it over the whole column,
 //     computed by whichever warp of a 32-column tile finishes last (an arrival
 //     counter per tile; no warp ever waits for another).
@@ -24,13 +26,16 @@ namespace edt {
 
 constexpr int K1_WARPS = 4;
 
-ColGeom col_geom(int rows, int64_t cols)
+ColGeom col_geom(int rows, int64_t cols, bool coarse)
 {
     ColGeom g;
     g.rows = rows;
     g.cols = cols;
     g.nb = (rows + 31) / 32;
-    g.nG = (g.nb + 31) / 32;
+    g.gs = 5;
+    if (!coarse)
+        while (g.gs > 0 && ((g.nb + (1 << (g.gs - 1)) - 1) >> (g.gs - 1)) <= 32) --g.gs;
+    g.nG = (g.nb + (1 << g.gs) - 1) >> g.gs;
     g.ntiles = (cols + 31) / 32;
     return g;
 }
@@ -58,6 +63,7 @@ ColScratch col_scratch_carve(void* base, const ColGeom& g)
     s.GAB = reinterpret_cast<uint32_t*>(p);
     p += align256((size_t)g.nG * c);
     s.cnt = reinterpret_cast<unsigned*>(p);
+    s.gs = g.gs;
     return s;
 }
 
@@ -109,8 +115,8 @@ __device__ __forceinline__ void group_scan(const ColGeom& g, const ColScratch& s
 {
     const int lane = threadIdx.x & 31;
     const int64_t W = g.cols;
-    const int b0 = G * 32;
-    const int nbg = min(32, g.nb - b0);
+    const int b0 = G << g.gs;
+    const int nbg = min(1 << g.gs, g.nb - b0);
     int last = NONE16, first = NONE16;
     for (int bl = 0; bl < nbg; ++bl) {
         uint32_t w = cw[bl][lane];
@@ -152,7 +158,8 @@ __device__ __forceinline__ void link_groups(const ColGeom& g, const ColScratch& 
     }
 }
 
-// The work of one warp: columns [32*tile, 32*tile + 32) x bands of group G.
+// The work of one warp: columns [32*tile, 32*tile + 32) x bands of group G
+// (bands G << gs .. (G + 1) << gs, at most 32).
 // cw and upS are this warp's 32 x 32 shared scratch tiles.  With PAIR the
 // warp serves both transforms from one read of the mask: s gets the summaries
 // with the nonzero bytes as sources, s1 those with the zero bytes (the column
@@ -167,8 +174,8 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
     const int64_t W = g.cols;
     const int64_t col0 = tile * 32;
     const int64_t col = col0 + lane;
-    const int b0 = G * 32;
-    const int nbg = min(32, g.nb - b0);
+    const int b0 = G << g.gs;
+    const int nbg = min(1 << g.gs, g.nb - b0);
     const int ncols = (W - col0) < 32 ? (int)(W - col0) : 32;
     const uint32_t colvalid = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
     const bool invert_in = !PAIR && mode == EDT_TO_BACKGROUND;

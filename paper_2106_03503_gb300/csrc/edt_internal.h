@@ -13,7 +13,7 @@ namespace edt {
 // scanned axis).  All arrays are uint32 in device memory, `cols` wide:
 //   C    [nb][cols]  column-bit words, bit r = row 32*band + r is a source
 //   U    [nb][cols]  nearest source row above | below << 16 of each band,
-//                    looking only inside the band's group of 32 bands
+//                    looking only inside the band's group (1 << gs bands)
 //                    (0xFFFF = none in the group)
 //   GFL  [nG][cols]  first | last << 16 source row of each group
 //   GAB  [nG][cols]  nearest source row above | below << 16 of each group,
@@ -25,17 +25,23 @@ struct ColScratch {
     uint32_t* GFL;
     uint32_t* GAB;
     unsigned* cnt;
+    int gs;        // bands per group = 1 << gs (the group of band b is b >> gs)
 };
 
 struct ColGeom {
     int rows;
     int64_t cols;
     int nb;        // bands of 32 rows
-    int nG;        // groups of 32 bands
+    int gs;        // bands per group = 1 << gs
+    int nG;        // groups of 1 << gs bands (at most 32)
     int64_t ntiles;  // tiles of 32 columns
 };
 
-ColGeom col_geom(int rows, int64_t cols);
+// Geometry of an image of `rows` x `cols` for the column pass.  Groups are
+// as small as possible while a column has at most 32 of them (more warps, each
+// with a shorter chain of bands); `coarse` keeps 32 bands per group (the
+// batch plans size their scratch for that).
+ColGeom col_geom(int rows, int64_t cols, bool coarse = false);
 size_t col_scratch_bytes(const ColGeom& g);
 ColScratch col_scratch_carve(void* base, const ColGeom& g);
 

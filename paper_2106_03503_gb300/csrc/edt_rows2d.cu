@@ -101,7 +101,7 @@ __device__ __forceinline__ void stage_band(const ColScratch& s, int b, int H, in
 {
     const uint32_t* Cb = s.C + (int64_t)b * W;
     const uint32_t* Ub = s.U + (int64_t)b * W;
-    const uint32_t* GABg = s.GAB + (int64_t)(b >> 5) * W;
+    const uint32_t* GABg = s.GAB + (int64_t)(b >> s.gs) * W;
     const int rows = min(32, H - b * 32);
     const uint32_t invalid = rows >= 32 ? 0u : (FULL << rows);
     const int Wr = (W + 31) & ~31;

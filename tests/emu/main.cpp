@@ -158,7 +158,7 @@ int main(int argc, char** argv)
         const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
         int bad = 0, cases = 0, run = 0;
         const int shapes[][2] = {{1, 1}, {1, 9}, {9, 1}, {5, 7}, {33, 31}, {64, 100}, {130, 70}, {40, 513},
-                                 {3, 2048}, {2, 8200}, {300, 40}, {17, 14336}};
+                                 {3, 2048}, {2, 8200}, {300, 40}, {17, 14336}, {1100, 33}};
         for (auto& sh : shapes)
             for (double p : {0.0, 0.003, 0.05, 1.0}) {
                 const int c = cases++;
@@ -173,7 +173,7 @@ int main(int argc, char** argv)
         const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
         int bad = 0, cases = 0, run = 0;
         const int shapes[][2] = {{1, 1}, {1, 9}, {9, 1}, {5, 7}, {33, 31}, {64, 100}, {40, 513}, {3, 2048},
-                                 {2, 8192}, {9, 8200}, {2, 16384}};
+                                 {2, 8192}, {9, 8200}, {2, 16384}, {1100, 33}};
         for (auto& sh : shapes)
             for (double p : {0.0, 0.003, 0.05, 1.0}) {
                 const int c = cases++;
@@ -187,7 +187,8 @@ int main(int argc, char** argv)
     if (argc > 1 && !strcmp(argv[1], "3d")) {
         int bad = 0, cases = 0;
         const int shapes[][3] = {{1, 1, 1}, {3, 5, 7}, {1, 40, 50}, {40, 1, 50}, {40, 50, 1},
-                                 {32, 33, 31}, {33, 32, 65}, {70, 17, 129}, {9, 17, 1000}, {5, 300, 40}};
+                                 {32, 33, 31}, {33, 32, 65}, {70, 17, 129}, {9, 17, 1000}, {5, 300, 40},
+                                 {1100, 2, 3}};
         for (auto& sh : shapes)
             for (double p : {0.001, 0.05, 0.5})
                 for (int mode = 0; mode < 2; ++mode) {
@@ -198,7 +199,7 @@ int main(int argc, char** argv)
         return bad != 0;
     }
     const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
-    const int Hs[] = {1, 2, 33, 64, 100};
+    const int Hs[] = {1, 2, 33, 64, 100, 1100, 2100};
     const int Ws[] = {1, 5, 16, 31, 32, 48, 100, 513, 1024, 2048, 2052, 4100, 8192};
     const double ps[] = {0.0, 0.001, 0.02, 0.3, 1.0};
     int cases = 0, run = 0, bad = 0;

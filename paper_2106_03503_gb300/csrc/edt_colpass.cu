@@ -82,9 +82,12 @@ __device__ __forceinline__ uint32_t nz_bits16(uint4 a)
            (nz_bits4(a.w) << 12);
 }
 
-// Source bits of the 32 bytes at p (only the first ncols are valid).
+// Source bits of the 32 bytes at p (only the first ncols are valid).  VEC:
+// p is 16-byte aligned.  al4: the mask starts on a 4-byte boundary, so the
+// aligned word holding byte p (and the bytes before p in it) lies inside the
+// mask.
 template <bool VEC>
-__device__ __forceinline__ uint32_t load_row_bits(const uint8_t* __restrict__ p, int ncols)
+__device__ __forceinline__ uint32_t load_row_bits(const uint8_t* __restrict__ p, int ncols, bool al4)
 {
     if (VEC && ncols == 32) {
         const uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
@@ -94,6 +97,22 @@ __device__ __forceinline__ uint32_t load_row_bits(const uint8_t* __restrict__ p,
     if (VEC && ncols == 16) {
         const uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
         return nz_bits16(a);
+    }
+    if (!VEC && al4 && ncols == 32) {
+        // 8 aligned words from the word holding byte p, the last o = p mod 4
+        // bytes one by one (never past byte 31), realigned by funnel shifts
+        const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(3);
+        const int o = (int)(reinterpret_cast<uintptr_t>(p) & 3);
+        const uint32_t* q = reinterpret_cast<const uint32_t*>(a);
+        uint32_t w[9];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = __ldcs(q + i);
+        w[8] = 0u;
+        for (int t = 0; t < o; ++t) w[8] |= (uint32_t)__ldcs(p + 32 - o + t) << (8 * t);
+        uint32_t bits = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) bits |= nz_bits4(__funnelshift_r(w[i], w[i + 1], 8 * o)) << (4 * i);
+        return bits;
     }
     uint32_t bits = 0;
     for (int t = 0; t < ncols; ++t) bits |= (uint32_t)(__ldcs(p + t) != 0) << t;
@@ -179,6 +198,7 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
     const int ncols = (W - col0) < 32 ? (int)(W - col0) : 32;
     const uint32_t colvalid = ncols >= 32 ? FULL : ((1u << ncols) - 1u);
     const bool invert_in = !PAIR && mode == EDT_TO_BACKGROUND;
+    const bool al4 = (reinterpret_cast<uintptr_t>(mask) & 3) == 0;
 
     // (1) source bits of 32 rows x 32 columns per band, transposed by ballots
     for (int bl = 0; bl < nbg; bl += 4) {
@@ -188,7 +208,7 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
             const int row = (b0 + bl + u) * 32 + lane;
             src[u] = 0;
             if (bl + u < nbg && row < g.rows) {
-                src[u] = load_row_bits<VEC>(mask + (int64_t)row * W + col0, ncols);
+                src[u] = load_row_bits<VEC>(mask + (int64_t)row * W + col0, ncols, al4);
                 if (invert_in) src[u] = ~src[u];
                 src[u] &= colvalid;
             }

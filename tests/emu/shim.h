@@ -49,6 +49,11 @@ inline float __int_as_float(int x) { float f; memcpy(&f, &x, 4); return f; }
 inline float __uint_as_float(uint32_t x) { float f; memcpy(&f, &x, 4); return f; }
 inline int __float_as_int(float f) { int x; memcpy(&x, &f, 4); return x; }
 inline uint32_t __float_as_uint(float f) { uint32_t x; memcpy(&x, &f, 4); return x; }
+inline unsigned __funnelshift_r(unsigned lo, unsigned hi, unsigned sh)
+{
+    const uint64_t v = ((uint64_t)hi << 32) | lo;
+    return (unsigned)(v >> (sh & 31));
+}
 inline unsigned __vcmpne4(unsigned a, unsigned b)
 {
     unsigned r = 0;

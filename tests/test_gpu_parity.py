@@ -181,3 +181,23 @@ def test_host_buffer_calls_match_device_calls(shape):
         for a, b in ((hDo, Do), (hFo, Fo), (hDb, Db), (hFb, Fb)):
             assert torch.equal(a, b.cpu())
         np.testing.assert_array_equal(hDo.numpy(), oracle.edt(m_np, 0)[0])
+
+
+@pytest.mark.parametrize("shape", [(70, 1000), (33, 4100), (40, 8192)])
+@pytest.mark.parametrize("offset", [0, 1, 2, 3, 4, 8])
+def test_mask_alignments(shape, offset):
+    """Masks that start 16-, 8-, 4-, 2- and 1-byte aligned (a view into a
+    larger buffer): the column pass reads them with vector, aligned-word or
+    byte loads, with the same result."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    m_np = inputs.bernoulli_mask(shape, 0.02, 17 + offset)
+    n = m_np.size
+    buf = torch.full((n + 16,), 7, dtype=torch.uint8, device="cuda")
+    buf[offset:offset + n] = torch.from_numpy(m_np.reshape(-1)).cuda()
+    m = buf[offset:offset + n].view(shape)
+    for mode in (0, 1):
+        D, F = edt.feature(m, mode)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(D.cpu().numpy(), oracle.edt(m_np, mode)[0])
+        assert feature_valid_fast(m_np, mode, D.cpu().numpy(), F.cpu().numpy()) is None

@@ -11,9 +11,9 @@
 //     loads 32 consecutive bytes of its own row; ballot t transposes byte t of
 //     all 32 rows into the word of column t);
 //   - per band, the nearest source row above and below it inside its group of
-//     bands (the smallest power of two, at most 32, that leaves a column at
-//     most 32 groups, so that small images still give many warps), from a
-//     forward and a backward scan over the group's words;
+//     bands (32, or fewer for images too small to give 4096 warp units, never
+//     more than 32 groups to a column), from a forward and a backward scan
+//     over the group's words;
 //   - per group, the nearest source above and below it over the whole column,
 //     computed by whichever warp of a 32-column tile finishes last (an arrival
 //     counter per tile; no warp ever waits for another).
@@ -32,11 +32,15 @@ ColGeom col_geom(int rows, int64_t cols, bool coarse)
     g.rows = rows;
     g.cols = cols;
     g.nb = (rows + 31) / 32;
-    g.gs = 5;
-    if (!coarse)
-        while (g.gs > 0 && ((g.nb + (1 << (g.gs - 1)) - 1) >> (g.gs - 1)) <= 32) --g.gs;
-    g.nG = (g.nb + (1 << g.gs) - 1) >> g.gs;
     g.ntiles = (cols + 31) / 32;
+    // smaller groups (more warps, each walking fewer bands) only while the
+    // image gives fewer than 4096 warp units: finer groups also make the
+    // consumers fall back to the group summaries more often
+    g.gs = 5;
+    auto groups = [&](int gs) { return (g.nb + (1 << gs) - 1) >> gs; };
+    if (!coarse)
+        while (g.gs > 0 && g.ntiles * groups(g.gs) < 4096 && groups(g.gs - 1) <= 32) --g.gs;
+    g.nG = groups(g.gs);
     return g;
 }
 

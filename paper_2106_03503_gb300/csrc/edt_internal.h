@@ -37,10 +37,10 @@ struct ColGeom {
     int64_t ntiles;  // tiles of 32 columns
 };
 
-// Geometry of an image of `rows` x `cols` for the column pass.  Groups are
-// as small as possible while a column has at most 32 of them (more warps, each
-// with a shorter chain of bands); `coarse` keeps 32 bands per group (the
-// batch plans size their scratch for that).
+// Geometry of an image of `rows` x `cols` for the column pass.  Groups have
+// 32 bands, or fewer (down to 1) while the image gives fewer than 4096 warp
+// units and a column keeps at most 32 groups; `coarse` keeps 32 bands per
+// group (the batch plans size their scratch for that).
 ColGeom col_geom(int rows, int64_t cols, bool coarse = false);
 size_t col_scratch_bytes(const ColGeom& g);
 ColScratch col_scratch_carve(void* base, const ColGeom& g);

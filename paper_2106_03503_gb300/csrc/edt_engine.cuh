@@ -37,9 +37,11 @@
 //       value there; owners move right monotonically with the position, and
 //       along the hull the values at a fixed position are unimodal, so a walk
 //       finds them.  Each lane writes
-//       its values 8 positions at a time: a row line as two 16-byte stores
-//       per array (one whole 32-byte sector), a column line as single stores
-//       that are coalesced across the 32 neighbouring lines.
+//       its values 8 positions at a time: a row line as one 32-byte store
+//       per array (a whole sector; 16-byte or single stores where the row
+//       layout does not allow it) or, for rows up to 2048 wide, through a TMA
+//       box of the warp's 32 rows; a column line as single stores that are
+//       coalesced across the 32 neighbouring lines.
 #pragma once
 
 #include <cstdint>

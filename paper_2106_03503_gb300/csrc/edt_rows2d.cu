@@ -233,7 +233,7 @@ static cudaError_t launch_rows(int H, int W, const RowJob& J0, const RowJob* J1,
     memset(m, 0, sizeof(m));
     const RowJob* jobs[2] = {&J0, J1};
     // TMA stores where the shared memory still allows two blocks per SM
-    // (widths up to 2048); per-lane 16-byte stores otherwise
+    // (widths up to 2048); per-lane 32-byte stores otherwise
     bool tma = W <= 2048;
     for (int k = 0; k < 2 && tma; ++k) {
         if (!jobs[k]) continue;

@@ -472,6 +472,22 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
+    # serving first of all, in the process's fresh state: its latencies
+    # depend on host-side state that the other measurements leave behind (in
+    # full runs measured after them, p99 was 3 to 5 times higher); no Python
+    # garbage collection pauses inside its polling loop
+    serve_result = None
+    if args.extras and rank == 0 and not args.profile:
+        import gc
+        gc.collect()
+        gc.disable()
+        try:
+            serve_result = measure_serve(edt, torch)
+        except Exception as exc:  # noqa: BLE001
+            serve_result = {"error": repr(exc)}
+        finally:
+            gc.enable()
+
     mask_np = inputs.discs_8192()
     mask = torch.from_numpy(mask_np).to(dev)
     D0 = torch.empty((H, W), dtype=torch.int32, device=dev)
@@ -542,18 +558,7 @@ def run_gpu(args, rank, world, local_rank):
 
     extras = {}
     if args.extras and rank == 0:
-        # serving first: its latencies depend most on host-side state (pinned
-        # buffers, pools) that the other measurements leave behind; no
-        # Python garbage collection pauses inside its polling loop
-        import gc
-        gc.collect()
-        gc.disable()
-        try:
-            extras["serve"] = measure_serve(edt, torch)
-        except Exception as exc:
-            extras["serve"] = {"error": repr(exc)}
-        finally:
-            gc.enable()
+        extras["serve"] = serve_result
         try:
             extras["small"] = measure_small(edt, torch, dev)
         except Exception as exc:  # noqa: BLE001

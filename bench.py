@@ -176,6 +176,16 @@ def cpu_oracle_rate(mask, repeats=1):
     return 2 * mask.size * repeats / dt / 1e9, dt
 
 
+def oracle_beside(fn, pixels, sample):
+    """The CPU oracle (single thread, this host) timed on a bounded sample
+    of an extra's workload: {"value": Gpixel/s, "sample": ..., "cores": 1}."""
+    t0 = time.perf_counter()
+    fn()
+    dt = time.perf_counter() - t0
+    return {"value": pixels / dt / 1e9, "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
+            "sample": sample, "seconds": dt}
+
+
 def measure_batch(edt, torch, dev, reps=5):
     """4096 masks (sides 64..1024, densities log-uniform 0.001..0.1): one
     edt_batch graph replay (job table prepared once, as for a fixed batch
@@ -215,12 +225,17 @@ def measure_batch(edt, torch, dev, reps=5):
     prepared = plan.prepare(jobs)            # the job table, filled once for the fixed batch layout
     t_batch = timed(lambda: plan.run(prepared))
     plan.close()
+    import oracle
+    sub = masks_np[:256]
+    cpu = oracle_beside(lambda: [oracle.edt(m, 0) for m in sub], sum(m.size for m in sub),
+                        "the first 256 of the 4096 masks, to object")
     return {"workload": "4096 2D masks, H and W uniform in [64, 1024], Bernoulli density "
                         "log-uniform in [0.001, 0.1] (seed 4), to-object, D+F",
             "pixels": px, "plain_ms": t_plain, "batched_ms": t_batch,
             "plain_gpx_s": px / (t_plain / 1e3) / 1e9, "batched_gpx_s": px / (t_batch / 1e3) / 1e9,
             "speedup": t_plain / t_batch,
-            "plain": "one edt_feature call per mask from Python (ctypes) on one stream"}
+            "plain": "one edt_feature call per mask from Python (ctypes) on one stream",
+            "cpu_oracle": cpu}
 
 
 def measure_volume(edt, torch, dev, reps=10):
@@ -247,7 +262,11 @@ def measure_volume(edt, torch, dev, reps=10):
     kern = {k: edt.trace_read(k)[0] / reps for k in ("k_colbits", "k_ypass3d", "k_xpass3d")}
     edt.trace_enable(False)
     n = m.numel()
-    return {"workload": "3D 512^3 N(0,1) noise smoothed by a Gaussian (sigma 4, periodic), "
+    import oracle
+    vs = inputs.smoothed_noise_volume((128, 128, 128), 4.0, 3)
+    cpu = oracle_beside(lambda: oracle.edt(vs, 0), vs.size, "128^3 volume of the same recipe, to object")
+    return {"cpu_oracle": cpu,
+            "workload": "3D 512^3 N(0,1) noise smoothed by a Gaussian (sigma 4, periodic), "
                         "thresholded at 0 (seed 3); to object; D+F",
             "voxels": n, "ms_per_transform": ms, "gvox_s": n / (ms / 1e3) / 1e9,
             "effective_gbs_9B_per_vox": 9 * n / (ms / 1e3) / 1e9, "kernel_ms": kern}
@@ -285,11 +304,15 @@ def measure_small(edt, torch, dev, calls=2000):
     back_to_back = 1e6 * (time.perf_counter() - t0) / calls
     gpu.sort()
     host.sort()
+    import oracle
+    small_np = inputs.points_512()
+    cpu = oracle_beside(lambda: [oracle.edt(small_np, 0) for _ in range(10)], 10 * small_np.size,
+                        "the same 512^2 image, 10 calls")
     q = lambda v, f: v[min(len(v) - 1, int(round(f * (len(v) - 1))))]  # noqa: E731
     return {"workload": "2D 512x512 Bernoulli p=0.01 (seed 1), to object, D+F, plain edt_feature calls",
             "calls": calls, "gpu_us_p50": q(gpu, 0.5), "gpu_us_p99": q(gpu, 0.99),
             "host_enqueue_us_p50": q(host, 0.5), "host_enqueue_us_p99": q(host, 0.99),
-            "back_to_back_us_per_call": back_to_back,
+            "back_to_back_us_per_call": back_to_back, "cpu_oracle": cpu,
             "gpx_s_back_to_back": m.numel() / (back_to_back * 1e-6) / 1e9}
 
 
@@ -325,7 +348,13 @@ def measure_nedt(edt, torch, dev, mask_np, kind, reps=20):
     edt.trace_enable(False)
     ms = total / reps
     px = 2 * m.numel()
-    return {"workload": f"{kind} DT of the 8192x8192 discs mask, to object and to background per step, int32 D",
+    import oracle
+    band = mask_np[:1024]
+    ofn = oracle.cityblock if kind == "cityblock" else oracle.chamfer43
+    cpu = oracle_beside(lambda: (ofn(band, 0), ofn(band, 1)), 2 * band.size,
+                        "rows 0..1023 of the discs mask, both source classes (two raster scans, Sec. 2)")
+    return {"cpu_oracle": cpu,
+            "workload": f"{kind} DT of the 8192x8192 discs mask, to object and to background per step, int32 D",
             "ms_per_step": ms, "gpx_s": px / (ms / 1e3) / 1e9,
             "effective_gbs_5B_per_px": 5 * px / (ms / 1e3) / 1e9, "kernel_ms_per_transform": k_ms}
 

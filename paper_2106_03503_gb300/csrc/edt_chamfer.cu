@@ -14,11 +14,11 @@
 //               min_{r in the column of p} E(r) + 3 |r - p| ),
 // where every candidate is the cost of a real path and the cheapest path is
 // among them.  Passes:
-//   (1) k_shear copies the sources into two sheared images (H x SW bytes):
-//       the column v of the first is the diagonal j - i = v - (H - 1), the
-//       column u of the second the anti-diagonal i + j = u;
-//   (2) the column-bit kernel of the Euclidean transform runs on each, giving
-//       the nearest source along every diagonal;
+//   (1)+(2) the column-bit kernel of the Euclidean transform runs on two
+//       sheared views of the mask (H x SW; the view's column v is the
+//       diagonal j - i = v - (H - 1), resp. the anti-diagonal i + j = v),
+//       reading the mask rows at shifted columns, and gives the nearest
+//       source along every diagonal;
 //   (3) k_chamfer_rows stages the sheared columns of 16 rows in shared
 //       memory, computes E and the row term as two prefix minima (weight 3),
 //       and writes the row term to D and E to a scratch image;
@@ -35,34 +35,6 @@ constexpr int CH_BIG = 1 << 29;       // no source
 constexpr int CH_CHUNK = 128;         // rows per chunk of the column kernels
 
 size_t chamfer_sheared_width(int H, int W) { return ((size_t)W + H - 1 + 31) & ~size_t(31); }
-
-// (1) 4 bytes of both sheared images per thread; 1 = source.
-__global__ void k_shear(const uint8_t* __restrict__ mask, int H, int W, int SW, int mode,
-                        uint8_t* __restrict__ Sd, uint8_t* __restrict__ Sa)
-{
-    const int64_t quads = (int64_t)H * (SW / 4);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < quads;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q / (SW / 4));
-        const int v0 = (int)(q - (int64_t)i * (SW / 4)) * 4;
-        uint32_t d = 0u, a = 0u;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int jd = v0 + t + i - (H - 1);      // diagonal j - i = v - (H - 1)
-            const int ja = v0 + t - i;                // anti-diagonal i + j = u
-            if (jd >= 0 && jd < W) {
-                const uint8_t m = mask[(int64_t)i * W + jd];
-                d |= (uint32_t)((mode == 0) ? (m != 0) : (m == 0)) << (8 * t);
-            }
-            if (ja >= 0 && ja < W) {
-                const uint8_t m = mask[(int64_t)i * W + ja];
-                a |= (uint32_t)((mode == 0) ? (m != 0) : (m == 0)) << (8 * t);
-            }
-        }
-        *reinterpret_cast<uint32_t*>(Sd + (int64_t)i * SW + v0) = d;
-        *reinterpret_cast<uint32_t*>(Sa + (int64_t)i * SW + v0) = a;
-    }
-}
 
 // Steps from row i (bit r of its band's word) to the nearest source of a
 // staged sheared column {w, up | dn << 16}; CH_BIG when the column has none.
@@ -244,7 +216,7 @@ size_t chamfer_scratch_bytes(int H, int W)
     const ColGeom gs = col_geom(H, (int64_t)SW);
     const size_t nq = (H + CH_CHUNK - 1) / CH_CHUNK;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    return 2 * al((size_t)H * SW) + 2 * al(col_scratch_bytes(gs)) + al((size_t)H * W * 4) + 2 * al(nq * W * 4);
+    return 2 * al(col_scratch_bytes(gs)) + al((size_t)H * W * 4) + 2 * al(nq * W * 4);
 }
 
 cudaError_t launch_chamfer(const uint8_t* mask, int H, int W, int mode, int32_t* D, void* scratch,
@@ -255,10 +227,6 @@ cudaError_t launch_chamfer(const uint8_t* mask, int H, int W, int mode, int32_t*
     const ColGeom gs = col_geom(H, SW);
     const int nq = (H + CH_CHUNK - 1) / CH_CHUNK;
     char* p = static_cast<char*>(scratch);
-    uint8_t* Sd = reinterpret_cast<uint8_t*>(p);
-    p += al((size_t)H * SW);
-    uint8_t* Sa = reinterpret_cast<uint8_t*>(p);
-    p += al((size_t)H * SW);
     const ColScratch sd = col_scratch_carve(p, gs);
     p += al(col_scratch_bytes(gs));
     const ColScratch sa = col_scratch_carve(p, gs);
@@ -271,14 +239,12 @@ cudaError_t launch_chamfer(const uint8_t* mask, int H, int W, int mode, int32_t*
     cudaError_t e;
     if ((e = cudaMemsetAsync(sd.cnt, 0, (size_t)gs.ntiles * 4, stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(sa.cnt, 0, (size_t)gs.ntiles * 4, stream)) != cudaSuccess) return e;
-    if ((e = traced("k_shear", stream, [&] {
-             k_shear<<<sm_count * 8, 256, 0, stream>>>(mask, H, W, SW, mode, Sd, Sa);
-             return cudaGetLastError();
-         })) != cudaSuccess)
+    (void)sm_count;
+    if ((e = traced("k_colbits", stream, [&] { return launch_colbits_sheared(mask, gs, mode, sd, H, W, 1, stream); })) !=
+        cudaSuccess)
         return e;
-    if ((e = traced("k_colbits", stream, [&] { return launch_colbits(Sd, gs, 0, sd, stream); })) != cudaSuccess)
-        return e;
-    if ((e = traced("k_colbits", stream, [&] { return launch_colbits(Sa, gs, 0, sa, stream); })) != cudaSuccess)
+    if ((e = traced("k_colbits", stream, [&] { return launch_colbits_sheared(mask, gs, mode, sa, H, W, -1, stream); })) !=
+        cudaSuccess)
         return e;
     const unsigned blocks = (unsigned)(((H + 31) / 32) * (32 / CH_ROWS));
     const size_t smem = 2 * (size_t)(W + CH_ROWS) * sizeof(uint2);

@@ -123,6 +123,29 @@ __device__ __forceinline__ uint32_t load_row_bits(const uint8_t* __restrict__ p,
     return bits;
 }
 
+// Source bits of the 32 bytes of one image row at columns j0 .. j0+31 (a
+// sheared view: some of them may lie outside the row; `valid` gets the bits
+// of those inside).
+__device__ __forceinline__ uint32_t sheared_row_bits(const uint8_t* __restrict__ row, int64_t W, int64_t j0,
+                                                     bool al4, uint32_t& valid)
+{
+    if (j0 >= 0 && j0 + 32 <= W) {
+        valid = FULL;
+        return load_row_bits<false>(row + j0, 32, al4);
+    }
+    uint32_t bits = 0;
+    valid = 0;
+    if (j0 + 32 <= 0 || j0 >= W) return 0;  // wholly outside the row
+    for (int t = 0; t < 32; ++t) {
+        const int64_t j = j0 + t;
+        if (j >= 0 && j < W) {
+            valid |= 1u << t;
+            bits |= (uint32_t)(__ldcs(row + j) != 0) << t;
+        }
+    }
+    return bits;
+}
+
 // Rows of band `band` that lie inside the image, as a bit mask.
 __device__ __forceinline__ uint32_t band_rows_mask(const ColGeom& g, int band)
 {
@@ -188,10 +211,15 @@ __device__ __forceinline__ void link_groups(const ColGeom& g, const ColScratch& 
 // with the nonzero bytes as sources, s1 those with the zero bytes (the column
 // words of the second are the complement of s.C inside the image and are not
 // stored).
-template <bool VEC, bool PAIR>
+//
+// SHEAR (+1 or -1) reads a sheared view of an imgH x imgW mask instead: the
+// view's column v at row r is the image's column v + r - (imgH - 1) (SHEAR
+// +1: the diagonals j - i = const become columns) or v - r (SHEAR -1: the
+// anti-diagonals); pixels outside the image are no sources.
+template <bool VEC, bool PAIR, int SHEAR = 0>
 __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g, int mode,
                              const ColScratch& s, const ColScratch& s1, int64_t tile, int G,
-                             uint32_t (*cw)[32], uint32_t (*upS)[32])
+                             uint32_t (*cw)[32], uint32_t (*upS)[32], int imgH = 0, int64_t imgW = 0)
 {
     const int lane = threadIdx.x & 31;
     const int64_t W = g.cols;
@@ -212,9 +240,17 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
             const int row = (b0 + bl + u) * 32 + lane;
             src[u] = 0;
             if (bl + u < nbg && row < g.rows) {
-                src[u] = load_row_bits<VEC>(mask + (int64_t)row * W + col0, ncols, al4);
-                if (invert_in) src[u] = ~src[u];
-                src[u] &= colvalid;
+                if (SHEAR == 0) {
+                    src[u] = load_row_bits<VEC>(mask + (int64_t)row * W + col0, ncols, al4);
+                    if (invert_in) src[u] = ~src[u];
+                    src[u] &= colvalid;
+                } else {
+                    const int64_t j0 = col0 + (SHEAR > 0 ? (int64_t)row - (imgH - 1) : -(int64_t)row);
+                    uint32_t valid;
+                    src[u] = sheared_row_bits(mask + (int64_t)row * imgW, imgW, j0, al4, valid);
+                    if (invert_in) src[u] = ~src[u];
+                    src[u] &= valid & colvalid;
+                }
             }
         }
 #pragma unroll
@@ -264,6 +300,33 @@ k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s, C
     const int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp;
     if (gw >= g.ntiles * (int64_t)g.nG) return;  // whole warp; no block sync below
     colbits_warp<VEC, PAIR>(mask, g, mode, s, s1, gw % g.ntiles, (int)(gw / g.ntiles), cw[warp], upS[warp]);
+}
+
+// Column pass over a sheared view (see colbits_warp) of an imgH x imgW mask;
+// g is the view's geometry (imgH rows).
+template <int SHEAR>
+__global__ void __launch_bounds__(K1_WARPS * 32)
+k_colbits_shear(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s, int imgH, int64_t imgW)
+{
+    __shared__ uint32_t cw[K1_WARPS][32][32];
+    __shared__ uint32_t upS[K1_WARPS][32][32];
+    const int warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp;
+    if (gw >= g.ntiles * (int64_t)g.nG) return;  // whole warp; no block sync below
+    colbits_warp<false, false, SHEAR>(mask, g, mode, s, s, gw % g.ntiles, (int)(gw / g.ntiles), cw[warp],
+                                      upS[warp], imgH, imgW);
+}
+
+cudaError_t launch_colbits_sheared(const uint8_t* mask, const ColGeom& g, int mode, const ColScratch& s,
+                                   int imgH, int64_t imgW, int dir, cudaStream_t stream)
+{
+    const int64_t warps = g.ntiles * (int64_t)g.nG;
+    const int64_t blocks = (warps + K1_WARPS - 1) / K1_WARPS;
+    if (dir > 0)
+        k_colbits_shear<1><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s, imgH, imgW);
+    else
+        k_colbits_shear<-1><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s, imgH, imgW);
+    return cudaGetLastError();
 }
 
 // Persistent column pass over every job of a batch: warp units are numbered

@@ -62,6 +62,12 @@ cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch&
 // chosen sources.
 cudaError_t launch_cityblock_rows(int H, int W, const ColGeom& g, const ColScratch& s, int32_t* D,
                                   cudaStream_t stream);
+// Column pass over a sheared view of an imgH x imgW mask (g: the view's
+// geometry): dir +1 turns the diagonals j - i = const into columns (view
+// column v = j - i + imgH - 1), dir -1 the anti-diagonals (v = i + j).
+cudaError_t launch_colbits_sheared(const uint8_t* mask, const ColGeom& g, int mode, const ColScratch& s,
+                                   int imgH, int64_t imgW, int dir, cudaStream_t stream);
+
 // Chamfer 4-3 transform (Sec. 2.2): scratch size and the whole pass sequence.
 size_t chamfer_scratch_bytes(int H, int W);
 cudaError_t launch_chamfer(const uint8_t* mask, int H, int W, int mode, int32_t* D, void* scratch,

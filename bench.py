@@ -62,23 +62,28 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+# The files a kernel is built from (the launcher's translation unit and the
+# headers it includes): a traffic record stays valid while they are unchanged.
+KERNEL_SOURCES = {"k_rows2d": ("edt_rows2d.cu", "edt_engine.cuh", "edt_internal.h")}
+
+
+def kernel_sources_sha256(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2106_03503_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def profile_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if
     that summary was taken on the current kernel sources (hash match)."""
     try:
-        from paper_2106_03503_gb300 import build_lib
-        import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             rec = json.load(fh)
         entry = rec.get(kernel)
-        if not entry:
-            return None
-        h = hashlib.sha256()
-        for p in sorted(build_lib._sources()) + sorted(
-                f for f in build_lib._deps() if f.endswith((".cuh", ".h")) and "csrc" in f):
-            with open(p, "rb") as fh:
-                h.update(fh.read())
-        if entry.get("sources_sha256") != h.hexdigest():
+        if not entry or entry.get("sources_sha256") != kernel_sources_sha256(kernel):
             return None
         return entry.get("dram_bytes_per_launch_full_size")
     except Exception:
@@ -343,7 +348,7 @@ def measure_nedt(edt, torch, dev, mask_np, kind, reps=20):
         torch.cuda.synchronize()
         total += a.elapsed_time(b)
     names = (("k_colbits", "k_cityblock_rows") if kind == "cityblock" else
-             ("k_shear", "k_colbits", "k_chamfer_rows", "k_chamfer_cols"))
+             ("k_colbits", "k_chamfer_rows", "k_chamfer_cols"))
     k_ms = {k: edt.trace_read(k)[0] / (2 * reps) for k in names}
     edt.trace_enable(False)
     ms = total / reps
@@ -392,12 +397,18 @@ def measure_serve(edt, torch, n_jobs=600, warm=200, loads=(0.5, 0.8), seed=5):
         return t
 
     def reap(lats):
+        """Collect finished jobs; sleep briefly when none has finished, so
+        that polling does not keep the server's lock and a core busy."""
+        got = False
         for t in list(busy):
             r = srv.poll(t)
             if r is not None:
                 slot, n = busy.pop(t)
                 free.append(slot)
                 lats.append((r[0], n))
+                got = True
+        if not got:
+            time.sleep(20e-6)
 
     order = rng.integers(0, len(pool), size=n_jobs + warm)
 

@@ -44,6 +44,10 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int SERVE_PLAN_JOBS = 512;          // jobs per batched launch
+// pixels admitted to one stream at a time (beyond the first job): a batch's
+// tickets complete together, so a long backlog is split over the streams in
+// batches of a few milliseconds of work instead of going to one stream whole
+constexpr int64_t SERVE_BATCH_PIXELS = (int64_t)1 << 25;
 
 struct Pending {
     uint64_t ticket;
@@ -103,9 +107,9 @@ void CUDART_CB on_batch_done(void* arg)
 {
     Completion* c = static_cast<Completion*>(arg);
     edt_server* s = c->srv;
+    const auto now = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        const auto now = Clock::now();
         for (uint64_t t : c->tickets) {
             auto it = s->tickets.find(t);
             if (it == s->tickets.end()) continue;
@@ -244,9 +248,12 @@ void scheduler(edt_server* s)
         // admit in arrival order while the budget allows
         std::vector<Pending> batch;
         size_t bytes = 0;
+        int64_t px = 0;
         while (!s->queue.empty() && s->in_use + bytes + s->queue.front().bytes <= s->budget &&
-               batch.size() < (size_t)4 * SERVE_PLAN_JOBS) {
+               batch.size() < (size_t)4 * SERVE_PLAN_JOBS &&
+               (batch.empty() || px + s->queue.front().n <= SERVE_BATCH_PIXELS)) {
             bytes += s->queue.front().bytes;
+            px += s->queue.front().n;
             batch.push_back(s->queue.front());
             s->queue.pop_front();
         }

@@ -512,6 +512,10 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
+    if args.profile and args.profile_workload != "pair":
+        run_profile_workload(edt, torch, dev, args.profile_workload, args.steps)
+        return
+
     # serving first of all, in the process's fresh state: its latencies
     # depend on host-side state that the other measurements leave behind (in
     # full runs measured after them, p99 was 3 to 5 times higher); no Python
@@ -662,6 +666,31 @@ def run_gpu(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_profile_workload(edt, torch, dev, which: str, calls: int):
+    """The kernels of one extra workload and nothing else, `calls` times, for
+    ncu launch lists and captures: "nedt" = city-block and chamfer 4-3 of the
+    8192^2 discs mask, both source classes; "volume" / "volume256" = the 3-D
+    transform (to object, D + F) of the 512^3 / 256^3 smoothed-noise volume."""
+    from paper_2106_03503_gb300 import inputs
+    if which == "nedt":
+        m = torch.from_numpy(inputs.discs_8192()).to(dev)
+        D = torch.empty(m.shape, dtype=torch.int32, device=dev)
+        for _ in range(calls):
+            for mode in (0, 1):
+                edt.cityblock(m, mode, out=D)
+                edt.chamfer43(m, mode, out=D)
+    else:
+        n = 512 if which == "volume" else 256
+        m_np = inputs.blobs_512cube() if n == 512 else inputs.smoothed_noise_volume((n, n, n), 4.0, 3)
+        m = torch.from_numpy(m_np).to(dev)
+        D = torch.empty(m.shape, dtype=torch.int32, device=dev)
+        F = torch.empty_like(D)
+        for _ in range(calls):
+            edt.feature(m, 0, out=(D, F, None))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": "ok", "workload": which, "calls": calls}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,6 +701,8 @@ def main():
                     help="skip the batch and serving measurements")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus --steps steps of the workload only (for ncu)")
+    ap.add_argument("--profile-workload", default="pair", choices=["pair", "nedt", "volume", "volume256"],
+                    help="with --profile: the headline pair (default) or one extra workload, --steps calls")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

@@ -68,11 +68,17 @@ KERNEL_SOURCES = {"k_rows2d": ("edt_rows2d.cu", "edt_engine.cuh", "edt_internal.
 
 
 def kernel_sources_sha256(kernel: str) -> str:
+    """SHA-256 of the kernel's sources with comments and whitespace runs
+    removed (a comment edit does not change the kernel)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_2106_03503_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2106_03503_gb300", "csrc", name)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()
 
 

@@ -1,5 +1,5 @@
 """CPU oracle for the exact squared Euclidean distance transform (and the
-city-block and chamfer 4-3 transforms of Section 2).
+city-block, chamfer 4-3 and Danielsson transforms of Section 2).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` use this package; the CUDA library and its Python
@@ -78,6 +78,9 @@ def _load():
             fn = getattr(lib, name)
             fn.restype = ctypes.c_int
             fn.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p]
+        lib.oracle_danielsson2d.restype = ctypes.c_int
+        lib.oracle_danielsson2d.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            i32p, i32p, i32p]
         _lib = lib
         return lib
 
@@ -189,6 +192,23 @@ def cityblock(mask, mode: int = TO_OBJECT, stop_after_forward: bool = False):
 def cityblock_4scan(mask, mode: int = TO_OBJECT, stop_after_columns: bool = False):
     """City-block transform of Sec. 2.1 by the four scans (columns, then rows)."""
     return _nedt("oracle_cityblock2d_4scan", mask, mode, stop_after_columns)
+
+
+def danielsson(mask, mode: int = TO_OBJECT, stop_after_forward: bool = False):
+    """Danielsson's approximate Euclidean transform, Sec. 2.3 (two scans of
+    relative-position propagation): (D, DY, DX), D = DY^2 + DX^2 in int32,
+    INT32_MAX and DY = DX = -1 where no position arrived."""
+    lib = _load()
+    m = _mask(mask)
+    assert m.ndim == 2
+    D = np.empty(m.shape, dtype=np.int32)
+    DY = np.empty(m.shape, dtype=np.int32)
+    DX = np.empty(m.shape, dtype=np.int32)
+    if lib.oracle_danielsson2d(_ptr(m, ctypes.c_uint8), m.shape[0], m.shape[1], int(mode),
+                               int(stop_after_forward), _ptr(D, ctypes.c_int32), _ptr(DY, ctypes.c_int32),
+                               _ptr(DX, ctypes.c_int32)) != 0:
+        raise MemoryError("oracle ran out of memory")
+    return D, DY, DX
 
 
 def chamfer43(mask, mode: int = TO_OBJECT, stop_after_forward: bool = False):

@@ -1,8 +1,9 @@
 /*
- * Oracle for the two non-Euclidean distance transforms of T. Strutz, "The
- * Distance Transform and its Computation -- An Introduction", Section 2: the
- * city-block distance transform (Sec. 2.1) and the chamfer 4-3 distance
- * transform (Sec. 2.2).
+ * Oracle for the propagation transforms of T. Strutz, "The Distance
+ * Transform and its Computation -- An Introduction", Section 2: the
+ * city-block distance transform (Sec. 2.1), the chamfer 4-3 distance
+ * transform (Sec. 2.2) and Danielsson's approximate Euclidean transform
+ * (Sec. 2.3, at the end of this file).
  *
  * TEST INFRASTRUCTURE ONLY, like edt_oracle.c: plain single-threaded C that
  * the tests, the smoke check and the benchmark's CPU baseline may load; the
@@ -136,5 +137,103 @@ int oracle_chamfer43_2d(const uint8_t *mask, int M, int L, int mode, int stop, i
             }
     put(d, (long)M * L, big, D);
     free(d);
+    return 0;
+}
+
+/*
+ * Sec. 2.3, Danielsson's approximate Euclidean transform in the form the
+ * paper gives it (after Grevera): every pixel carries a relative position
+ * (dy, dx) with non-negative components, (0, 0) on sources, none elsewhere.
+ * Looking at a neighbour, a pixel takes the neighbour's position with dy
+ * increased by one for a vertical step, dx for a horizontal one and both for
+ * a diagonal one, when dy^2 + dx^2 of that is strictly below its own.
+ * Forward scan, rows 1 .. M-1 (0-based; the first row is skipped), per row:
+ *   (a) every column: the upper neighbour;
+ *   (b) columns 1 .. L-1 left to right: the left, then the upper-left one;
+ *   (c) columns L-2 .. 0 right to left: the upper-right, then the right one.
+ * Backward scan, rows M-2 .. 0, mirrored vertically:
+ *   (a) every column: the lower neighbour;
+ *   (b) left to right: the left, then the lower-left one;
+ *   (c) right to left: the right, then the lower-right one.
+ * Readings: inside (c) of the forward scan the upper-right neighbour comes
+ * first, as in the paper's listing (its text names the right neighbour
+ * first); a single-row image is visited by neither scan, so only its
+ * sources get a position.
+ * Pins: Fig. 16(b) and 16(c) fix the passes, the increments and the strict
+ * comparison (a plant of any of those fails them), and the tests check the
+ * invariants below.  The order of the two looks inside (b) and (c) and the
+ * diagonal looks themselves do not change the example's result (they matter
+ * only at ties and in rare configurations): for those details parity is
+ * unpinned.
+ * stop = 1 returns the state after the forward scan (Fig. 16(b)).
+ * Out: D = dy^2 + dx^2 (INT32_MAX without a position), DY, DX (-1 there).
+ */
+typedef struct {
+    int64_t *dy, *dx;  /* -1 = no position yet */
+    int L;
+} RelPos;
+
+static int64_t rel_len(const RelPos *r, long p)
+{
+    return r->dy[p] < 0 ? INT64_MAX : r->dy[p] * r->dy[p] + r->dx[p] * r->dx[p];
+}
+
+/* let pixel p look at neighbour q, with the step (sy, sx) in {0, 1}^2 */
+static void take(RelPos *r, long p, long q, int sy, int sx)
+{
+    if (r->dy[q] < 0) return;
+    const int64_t ny = r->dy[q] + sy, nx = r->dx[q] + sx;
+    if (rel_len(r, p) > ny * ny + nx * nx) {
+        r->dy[p] = ny;
+        r->dx[p] = nx;
+    }
+}
+
+/* one row of a scan; v = -1 looks at the row above, +1 at the row below */
+static void danielsson_row(RelPos *r, int i, int v)
+{
+    const int L = r->L;
+    const long row = (long)i * L, nb = (long)(i + v) * L;
+    for (int j = 0; j < L; ++j) take(r, row + j, nb + j, 1, 0);
+    for (int j = 1; j < L; ++j) {
+        take(r, row + j, row + j - 1, 0, 1);
+        take(r, row + j, nb + j - 1, 1, 1);
+    }
+    for (int j = L - 2; j >= 0; --j) {
+        if (v < 0) {
+            take(r, row + j, nb + j + 1, 1, 1);
+            take(r, row + j, row + j + 1, 0, 1);
+        } else {
+            take(r, row + j, row + j + 1, 0, 1);
+            take(r, row + j, nb + j + 1, 1, 1);
+        }
+    }
+}
+
+int oracle_danielsson2d(const uint8_t *mask, int M, int L, int mode, int stop, int32_t *D, int32_t *DY,
+                        int32_t *DX)
+{
+    const long n = (long)M * L;
+    RelPos r;
+    r.L = L;
+    r.dy = (int64_t *)malloc(sizeof(int64_t) * (n ? n : 1));
+    r.dx = (int64_t *)malloc(sizeof(int64_t) * (n ? n : 1));
+    if (!r.dy || !r.dx) {
+        free(r.dy);
+        free(r.dx);
+        return 1;
+    }
+    for (long p = 0; p < n; ++p) r.dy[p] = r.dx[p] = is_source(mask, p, mode) ? 0 : -1;
+    for (int i = 1; i < M; ++i) danielsson_row(&r, i, -1);
+    if (!stop)
+        for (int i = M - 2; i >= 0; --i) danielsson_row(&r, i, +1);
+    for (long p = 0; p < n; ++p) {
+        const int64_t len = rel_len(&r, p);
+        D[p] = len == INT64_MAX || len > INT32_MAX ? INT32_MAX : (int32_t)len;
+        DY[p] = (int32_t)r.dy[p];
+        DX[p] = (int32_t)r.dx[p];
+    }
+    free(r.dy);
+    free(r.dx);
     return 0;
 }

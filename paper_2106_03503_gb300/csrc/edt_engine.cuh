@@ -156,7 +156,12 @@ __host__ __device__ inline int band_seg_log2(int n, int max_nw)
     return lg;
 }
 
-// t is hidden between p < t < m on the hull of points (k, c_k).
+// t is hidden between p < t < m on the hull of points (k, c_k).  With
+// c_k = f(k) + k^2 and a = t - p, b = m - t, c = m - p this is
+// c f(t) - b f(p) - a f(m) - abc >= 0: the separating-line test of Maurer et
+// al. (the alternative the paper's Sec. 4 names), with >= in place of >.
+// The two differ only where the three parabolas meet in one point, which
+// changes a feature at a tie and never a distance.
 __device__ __forceinline__ bool hidden(int p, int cp, int t, int ct, int m, int cm)
 {
     return (long long)(cm - ct) * (long long)(t - p) <=

@@ -32,6 +32,16 @@ def keyed(name):
     return out
 
 
+def pairs(name):
+    """Grid of 'dy,dx' cells ('-' = none) as two int arrays (-1 = none)."""
+    dy, dx = [], []
+    for line in _lines(name):
+        cells = line.split()
+        dy.append([-1 if c == "-" else int(c.split(",")[0]) for c in cells])
+        dx.append([-1 if c == "-" else int(c.split(",")[1]) for c in cells])
+    return np.array(dy, dtype=np.int64), np.array(dx, dtype=np.int64)
+
+
 def six_object_mask():
     """Fig. 18(a) as a uint8 mask (1 = object)."""
     g = grid("fig18a_init.txt")

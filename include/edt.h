@@ -126,9 +126,9 @@ edt_status edt_cityblock2d(const uint8_t *mask, int H, int W, int mode,
  * pixels (a, b) of `mode` -- the cost of the cheapest path with steps of 3
  * (horizontal, vertical) and 4 (diagonal), the result of the paper's two
  * raster scans -- INT32_MAX when the image has no source.  Device pointers;
- * D is H x W int32, row-major; scratch (about 4.5 bytes per pixel plus
- * 2 bytes per pixel and row of sheared images) comes from the stream-ordered
- * pool.  Errors as edt_sq2d; rows wider than 14336 columns return
+ * D is H x W int32, row-major; scratch (about 4 bytes per pixel plus
+ * about 0.25 byte per position of each of the two sheared H x (W + H - 1)
+ * views the column passes run over) comes from the stream-ordered pool.  Errors as edt_sq2d; rows wider than 14336 columns return
  * EDT_ERR_TOO_LARGE (a block keeps two sheared column records of 8 bytes per
  * column of its rows in shared memory). */
 edt_status edt_chamfer43_2d(const uint8_t *mask, int H, int W, int mode,

@@ -519,7 +519,7 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     if args.profile and args.profile_workload != "pair":
-        run_profile_workload(edt, torch, dev, args.profile_workload, args.steps)
+        run_profile_workload(edt, torch, dev, args.profile_workload, args.steps, args.profile_jobs)
         return
 
     # serving first of all, in the process's fresh state: its latencies
@@ -672,13 +672,25 @@ def run_gpu(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def run_profile_workload(edt, torch, dev, which: str, calls: int):
+def run_profile_workload(edt, torch, dev, which: str, calls: int, jobs: int = 4096):
     """The kernels of one extra workload and nothing else, `calls` times, for
     ncu launch lists and captures: "nedt" = city-block and chamfer 4-3 of the
     8192^2 discs mask, both source classes; "volume" / "volume256" = the 3-D
-    transform (to object, D + F) of the 512^3 / 256^3 smoothed-noise volume."""
+    transform (to object, D + F) of the 512^3 / 256^3 smoothed-noise volume;
+    "batch" = one edt_batch replay of the first `jobs` masks of the 4096-mask
+    batch workload (to object, D + F)."""
     from paper_2106_03503_gb300 import inputs
-    if which == "nedt":
+    if which == "batch":
+        masks = [torch.from_numpy(m).to(dev) for m in inputs.batch_4096()[:jobs]]
+        outs = [(torch.empty(m.shape, dtype=torch.int32, device=dev),
+                 torch.empty(m.shape, dtype=torch.int32, device=dev)) for m in masks]
+        plan = edt.Plan(len(masks), sum(m.numel() for m in masks))
+        prepared = plan.prepare([(m, 0, D, F, None) for m, (D, F) in zip(masks, outs)])
+        for _ in range(calls):
+            plan.run(prepared)
+        torch.cuda.synchronize()
+        plan.close()
+    elif which == "nedt":
         m = torch.from_numpy(inputs.discs_8192()).to(dev)
         D = torch.empty(m.shape, dtype=torch.int32, device=dev)
         for _ in range(calls):
@@ -707,8 +719,10 @@ def main():
                     help="skip the batch and serving measurements")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus --steps steps of the workload only (for ncu)")
-    ap.add_argument("--profile-workload", default="pair", choices=["pair", "nedt", "volume", "volume256"],
+    ap.add_argument("--profile-workload", default="pair", choices=["pair", "nedt", "volume", "volume256", "batch"],
                     help="with --profile: the headline pair (default) or one extra workload, --steps calls")
+    ap.add_argument("--profile-jobs", type=int, default=4096,
+                    help="with --profile-workload batch: how many of the 4096 masks")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

@@ -62,6 +62,7 @@ inline unsigned __vcmpne4(unsigned a, unsigned b)
     return r;
 }
 template <class T> inline T __ldcs(const T* p) { return *p; }
+template <class T> inline T __ldg(const T* p) { return *p; }
 template <class T> inline T __ldcg(const T* p) { return *p; }
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 inline unsigned atomicAdd(unsigned* p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }

@@ -13,7 +13,8 @@ Prints one JSON line (rank 0).  `value` is whole-job Gpixel/s over the timed
 steps (CUDA events on the launching stream, L2 flushed between steps by
 writing a 256 MiB buffer, inputs resident in HBM).  `e2e` is the same metric
 through edt_feature_pair_host with pinned host buffers (the mask copy and the
-result copies in the timed region).  The step calls edt_feature_pair: one column pass and one row-pass
+result copies in the timed region), called from two host threads with a
+stream each (`one_call_at_a_time`: the same calls back to back).  The step calls edt_feature_pair: one column pass and one row-pass
 launch serve both transforms.  `roofline` is the row-pass kernel k_rows2d, timed live by libedt's
 event tracing, against the measured HBM copy bandwidth.  `cpu_baseline` is the
 CPU oracle timed on this host on one full step.  With --impl reference the
@@ -593,7 +594,7 @@ def run_gpu(args, rank, world, local_rank):
     hmask = torch.from_numpy(mask_np).pin_memory()
     hD = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
     hF = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(4, min(args.steps, 20)) & ~1
     host_out = ((hD[0], hF[0]), (hD[1], hF[1]))
     edt.feature_pair_host(hmask, out=host_out)
     barrier()
@@ -602,8 +603,43 @@ def run_gpu(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         edt.feature_pair_host(hmask, out=host_out)
     torch.cuda.synchronize()
+    e2e_serial, _ = whole_job_rate(1e3 * (time.perf_counter() - t0), px_step, e2e_steps, world,
+                                   reduce_max)
+    barrier()
+    # the same calls from two host threads, each with its own stream and
+    # pinned result buffers, so that one call's mask copy and kernels run
+    # while the other's results cross the host link (the call itself is
+    # synchronous); every step still copies its mask in and both results out
+    hD2 = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
+    hF2 = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
+    outs2 = [host_out, ((hD2[0], hF2[0]), (hD2[1], hF2[1]))]
+    streams2 = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    errors = []
+
+    def worker(k, n):
+        try:
+            torch.cuda.set_device(dev)
+            for _ in range(n):
+                edt.feature_pair_host(hmask, out=outs2[k], stream=streams2[k])
+        except Exception as exc:  # noqa: BLE001
+            errors.append(exc)
+
+    import threading
+    for k in range(2):                      # warm-up: both streams' pool blocks
+        worker(k, 1)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=worker, args=(k, e2e_steps // 2)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
     e2e_value, _ = whole_job_rate(1e3 * (time.perf_counter() - t0), px_step, e2e_steps, world,
                                   reduce_max)
+    if errors:
+        raise errors[0]
     barrier()
 
     extras = {}
@@ -662,7 +698,8 @@ def run_gpu(args, rank, world, local_rank):
                                        f"mask each), single-threaded C oracle, {cpu_s:.1f} s"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": H * W,
                     "d2h_bytes_per_step": 2 * 2 * 4 * H * W, "steps": e2e_steps,
-                    "api": "edt_feature_pair_host, pinned host buffers"},
+                    "api": "edt_feature_pair_host, pinned host buffers",
+                    "calls_in_flight": 2, "one_call_at_a_time": e2e_serial},
             "gpu_launches": k1_n + k2_n,
             "clocks": clocks,
             "extras": extras,

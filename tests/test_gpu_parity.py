@@ -183,6 +183,42 @@ def test_host_buffer_calls_match_device_calls(shape):
         np.testing.assert_array_equal(hDo.numpy(), oracle.edt(m_np, 0)[0])
 
 
+def test_concurrent_host_calls_from_two_threads():
+    """Two host threads, each with its own stream, masks and pinned buffers,
+    call edt_feature_pair_host at the same time (as bench.py's end-to-end
+    measurement does): the library's shared state (device setup, the copy
+    stream, the memory pool) must keep every result equal to the oracle's."""
+    import threading
+    import torch
+    from paper_2106_03503_gb300 import edt
+    shapes = [(1500, 2100), (700, 4100)]
+    masks = [inputs.bernoulli_mask(sh, 0.01, 900 + k) for k, sh in enumerate(shapes)]
+    want = [(oracle.edt(m, 0)[0], oracle.edt(m, 1)[0]) for m in masks]
+    errors = []
+
+    def worker(k):
+        try:
+            torch.cuda.set_device(0)
+            st = torch.cuda.Stream()
+            hm = torch.from_numpy(masks[k]).pin_memory()
+            for _ in range(4):
+                (Do, Fo), (Db, Fb) = edt.feature_pair_host(hm, stream=st)
+                np.testing.assert_array_equal(Do.numpy(), want[k][0])
+                np.testing.assert_array_equal(Db.numpy(), want[k][1])
+                for mode, (D, F) in enumerate(((Do, Fo), (Db, Fb))):
+                    assert feature_valid_fast(masks[k], mode, D.numpy(), F.numpy()) is None
+        except Exception as exc:  # noqa: BLE001
+            errors.append(exc)
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+
+
 @pytest.mark.parametrize("shape", [(70, 1000), (33, 4100), (40, 8192)])
 @pytest.mark.parametrize("offset", [0, 1, 2, 3, 4, 8])
 def test_mask_alignments(shape, offset):

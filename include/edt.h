@@ -168,7 +168,10 @@ edt_status edt_batch(edt_plan *plan, const edt_job *jobs, int n,
  * mem_budget_bytes, copies them in, groups the admitted jobs into batches,
  * runs them on n_streams streams so that batches overlap, copies results out
  * and completes the ticket.  Each result is identical to a plain edt_feature
- * call on the same mask. */
+ * call on the same mask.  The budget is taken from the device when the
+ * server is created (a memory pool of its own, grown to the budget less the
+ * batch plans' scratch) and given back by edt_serve_destroy; EDT_ERR_CUDA if
+ * the device cannot provide it. */
 typedef struct edt_server edt_server;
 
 edt_status edt_serve_create(edt_server **server, size_t mem_budget_bytes,

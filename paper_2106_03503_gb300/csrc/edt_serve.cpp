@@ -4,7 +4,7 @@
 // jobs and a set of CUDA streams, each owning a batch plan.  Whenever a stream
 // is idle and the head of the FIFO fits the device-memory budget, it admits
 // jobs in arrival order while they fit, allocates their device buffers from
-// the stream-ordered pool, and enqueues on that stream: the mask copies in,
+// the server's memory pool, and enqueues on that stream: the mask copies in,
 // one batched launch for the 2-D jobs a plan accepts (width <= 2048) and plain
 // transforms for the others (wider 2-D images, 3-D volumes), the result copies
 // out, the buffer frees, and a host callback that completes the tickets and
@@ -77,6 +77,7 @@ struct Completion;
 struct edt_server {
     int device = 0;
     int sm_count = 0;
+    cudaMemPool_t pool = nullptr;   // job buffers: the server's own pool, grown to the budget at creation
     size_t budget = 0;       // bytes available to job buffers
     size_t in_use = 0;
     int64_t plan_pixels = 0;
@@ -159,12 +160,12 @@ void launch_batch(edt_server* s, int si, std::vector<Pending>& batch, size_t byt
         const size_t n = (size_t)p.n;
         const bool batched = p.job.ndim == 2 && p.job.shape[1] <= BATCH_MAX_W &&
                              (int64_t)n <= s->plan_pixels;
-        if ((e = cudaMallocAsync((void**)&d.mask, n, st)) != cudaSuccess ||
-            (e = cudaMallocAsync((void**)&d.F, n * 4, st)) != cudaSuccess ||
-            (p.job.D && (e = cudaMallocAsync((void**)&d.D, n * 4, st)) != cudaSuccess) ||
-            (p.job.dist && (e = cudaMallocAsync((void**)&d.dist, n * 4, st)) != cudaSuccess) ||
+        if ((e = cudaMallocFromPoolAsync((void**)&d.mask, n, s->pool, st)) != cudaSuccess ||
+            (e = cudaMallocFromPoolAsync((void**)&d.F, n * 4, s->pool, st)) != cudaSuccess ||
+            (p.job.D && (e = cudaMallocFromPoolAsync((void**)&d.D, n * 4, s->pool, st)) != cudaSuccess) ||
+            (p.job.dist && (e = cudaMallocFromPoolAsync((void**)&d.dist, n * 4, s->pool, st)) != cudaSuccess) ||
             (!batched &&
-             (e = cudaMallocAsync(&d.scratch, scratch_bytes(p.job.ndim, p.job.shape), st)) != cudaSuccess)) {
+             (e = cudaMallocFromPoolAsync(&d.scratch, scratch_bytes(p.job.ndim, p.job.shape), s->pool, st)) != cudaSuccess)) {
             status = cuda_fail(e, "serve: device buffers");
             dev[k] = d;
             break;
@@ -302,6 +303,37 @@ extern "C" edt_status edt_serve_create(edt_server** out, size_t mem_budget_bytes
         return st;
     }
     s->budget = mem_budget_bytes - reserved;
+    // job buffers come from a pool of the server's own that keeps what is
+    // freed, takes no cross-stream dependencies to reuse it, and is grown to
+    // the budget here, so that no admitted job waits for the pool to map new
+    // memory
+    {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = s->device;
+        cudaError_t e = cudaMemPoolCreate(&s->pool, &props);
+        uint64_t keep = UINT64_MAX;
+        int no = 0;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+        void* warm = nullptr;
+        cudaStream_t st0 = s->slots[0].stream;
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&warm, s->budget, s->pool, st0);
+        if (e == cudaSuccess) e = cudaFreeAsync(warm, st0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
+        if (e != cudaSuccess) {
+            const edt_status err = cuda_fail(e, "serve: memory pool");
+            if (s->pool) cudaMemPoolDestroy(s->pool);
+            for (auto& slot : s->slots) {
+                edt_plan_destroy(slot.plan);
+                cudaStreamDestroy(slot.stream);
+            }
+            delete s;
+            return err;
+        }
+    }
     s->sched = std::thread(scheduler, s);
     *out = s;
     clear_error();
@@ -369,6 +401,7 @@ extern "C" edt_status edt_serve_destroy(edt_server* s)
         edt_plan_destroy(slot.plan);
         cudaStreamDestroy(slot.stream);
     }
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return EDT_OK;
 }

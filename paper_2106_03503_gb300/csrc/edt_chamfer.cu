@@ -21,10 +21,13 @@
 //       source along every diagonal;
 //   (3) k_chamfer_rows stages the sheared columns of 16 rows in shared
 //       memory, computes E and the row term as two prefix minima (weight 3),
-//       and writes the row term to D and E to a scratch image;
-//   (4) k_chamfer_cols_totals and k_chamfer_cols take the column term over
-//       chunks of 128 rows (chunk minima first, then each chunk with the
-//       minima of the chunks above and below it) and lower D to it.
+//       writes the row term to D and E to a scratch image, and per column
+//       the minima of E(m) - 3m and E(m) + 3m over its 16 rows;
+//   (4) k_chamfer_cols_carry turns those chunk minima into the minima over
+//       all chunks above / below each chunk, and k_chamfer_cols takes the
+//       column term of every 16-row chunk from its E values (in registers)
+//       and those carries, lowering D to it: one read of E and D, one write
+//       of D.
 #include "edt_engine.cuh"
 #include "edt_internal.h"
 
@@ -32,7 +35,7 @@ namespace edt {
 
 constexpr int CH_ROWS = 16;           // rows per block of the row kernel
 constexpr int CH_BIG = 1 << 29;       // no source
-constexpr int CH_CHUNK = 128;         // rows per chunk of the column kernels
+constexpr int CH_CHUNK = CH_ROWS;     // rows per chunk of the column kernels (one row block)
 
 size_t chamfer_sheared_width(int H, int W) { return ((size_t)W + H - 1 + 31) & ~size_t(31); }
 
@@ -71,7 +74,7 @@ __device__ __forceinline__ uint2 sheared_column(const ColScratch& s, int64_t SW,
 template <int SL>
 __global__ void __launch_bounds__(1024)
 k_chamfer_rows(int H, int W, int SW, ColScratch sd, ColScratch sa, int32_t* __restrict__ D,
-               int32_t* __restrict__ E)
+               int32_t* __restrict__ E, int* __restrict__ Tf, int* __restrict__ Tb)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sx[32], sy[32];
@@ -92,6 +95,9 @@ k_chamfer_rows(int H, int W, int SW, ColScratch sd, ColScratch sa, int32_t* __re
     }
     __syncthreads();
     const int jw = warp * 32 * SL;
+    int tf[SL], tb[SL];                                   // chunk minima of E(m) -/+ 3m
+#pragma unroll
+    for (int c = 0; c < SL; ++c) tf[c] = tb[c] = CH_BIG;
     for (int i = i0; i < i1; ++i) {
         const int r = i - base;
         int e[SL], px[SL], sq[SL];
@@ -107,6 +113,8 @@ k_chamfer_rows(int H, int W, int SW, ColScratch sd, ColScratch sa, int32_t* __re
                 ev = dm >= CH_BIG ? CH_BIG : 4 * dm;
             }
             e[c] = ev;
+            tf[c] = min(tf[c], ev - 3 * i);
+            tb[c] = min(tb[c], ev + 3 * i);
             // slice prefix of E(k) - 3k, continued from the previous slices
             int v = ev - 3 * j;
 #pragma unroll
@@ -162,51 +170,85 @@ k_chamfer_rows(int H, int W, int SW, ColScratch sd, ColScratch sa, int32_t* __re
         }
         __syncthreads();
     }
-}
-
-// (4a) per chunk of CH_CHUNK rows and column: min of E(m) - 3m and E(m) + 3m.
-__global__ void k_chamfer_cols_totals(int H, int W, const int32_t* __restrict__ E, int* __restrict__ Tf,
-                                      int* __restrict__ Tb)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int q = blockIdx.y;
-    if (j >= W) return;
-    int f = CH_BIG, bk = CH_BIG;
-    const int m1 = min(H, (q + 1) * CH_CHUNK);
-    for (int m = q * CH_CHUNK; m < m1; ++m) {
-        const int e = E[(int64_t)m * W + j];
-        f = min(f, e - 3 * m);
-        bk = min(bk, e + 3 * m);
+    const int64_t q = i0 / CH_CHUNK;
+#pragma unroll
+    for (int c = 0; c < SL; ++c) {
+        const int j = jw + 32 * c + lane;
+        if (j < W) {
+            Tf[q * W + j] = tf[c];
+            Tb[q * W + j] = tb[c];
+        }
     }
-    Tf[(int64_t)q * W + j] = f;
-    Tb[(int64_t)q * W + j] = bk;
 }
 
-// (4b) the column term of every pixel of a chunk, with the other chunks'
-// minima as carries; D becomes min(row term, column term), INT32_MAX where
-// no source exists.  (Keeping the term from below in shared memory instead
-// of a second pass over D was slower: 64 KB per 128 columns left too few
-// warps per SM for these sequential loops.)
-__global__ void k_chamfer_cols(int H, int W, const int32_t* __restrict__ E, const int* __restrict__ Tf,
-                               const int* __restrict__ Tb, int nq, int32_t* __restrict__ D)
+// (4a) per column, in place: Tf[q] becomes the minimum of E(m) - 3m over the
+// chunks above chunk q, Tb[q] that of E(m) + 3m over the chunks below it.  A
+// block of 32 warps takes 32 columns (lane x) and splits their chunks into 32
+// consecutive runs (warp y): each thread reduces its run, the runs' minima are combined through
+// shared memory, and each thread then rewrites its run with the carries.
+__global__ void __launch_bounds__(1024)
+k_chamfer_cols_carry(int W, int nq, int* __restrict__ Tf, int* __restrict__ Tb)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int q = blockIdx.y;
-    if (j >= W) return;
+    __shared__ int sf[32][33], sb[32][33];
+    const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + x;
+    const int q0 = (int)((int64_t)nq * y / 32), q1 = (int)((int64_t)nq * (y + 1) / 32);
+    int f = CH_BIG, b = CH_BIG;
+    if (j < W)
+        for (int q = q0; q < q1; ++q) {
+            f = min(f, Tf[q * (int64_t)W + j]);
+            b = min(b, Tb[q * (int64_t)W + j]);
+        }
+    sf[y][x] = f;
+    sb[y][x] = b;
+    __syncthreads();
     int cf = CH_BIG, cb = CH_BIG;
-    for (int k = 0; k < q; ++k) cf = min(cf, Tf[(int64_t)k * W + j]);
-    for (int k = q + 1; k < nq; ++k) cb = min(cb, Tb[(int64_t)k * W + j]);
-    const int m0 = q * CH_CHUNK, m1 = min(H, m0 + CH_CHUNK);
-    for (int m = m1 - 1; m >= m0; --m) {              // from below: -3m + min_{k>=m} E(k) + 3k
-        const int64_t o = (int64_t)m * W + j;
-        cb = min(cb, E[o] + 3 * m);
-        D[o] = min(D[o], -3 * m + cb);
+    for (int k = 0; k < y; ++k) cf = min(cf, sf[k][x]);
+    for (int k = y + 1; k < 32; ++k) cb = min(cb, sb[k][x]);
+    if (j >= W) return;                                  // no barrier below
+    for (int q = q0; q < q1; ++q) {
+        const int t = Tf[q * (int64_t)W + j];
+        Tf[q * (int64_t)W + j] = cf;
+        cf = min(cf, t);
     }
-    for (int m = m0; m < m1; ++m) {                    // from above: 3m + min_{k<=m} E(k) - 3k
-        const int64_t o = (int64_t)m * W + j;
-        cf = min(cf, E[o] - 3 * m);
-        const int d = min(D[o], 3 * m + cf);
-        D[o] = d >= CH_BIG / 2 ? INT32_MAX : d;
+    for (int q = q1 - 1; q >= q0; --q) {
+        const int t = Tb[q * (int64_t)W + j];
+        Tb[q * (int64_t)W + j] = cb;
+        cb = min(cb, t);
+    }
+}
+
+// (4b) the column term of every pixel of one chunk of CH_CHUNK rows: its E
+// values in registers, the minima from below as a suffix over them plus the
+// carry from the chunks below, the minima from above as a prefix plus the
+// carry from the chunks above; D becomes min(row term, column term),
+// INT32_MAX where no source exists.
+__global__ void k_chamfer_cols(int H, int W, const int32_t* __restrict__ E, const int* __restrict__ Cf,
+                               const int* __restrict__ Cb, int32_t* __restrict__ D)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (j >= W) return;
+    const int m0 = q * CH_CHUNK;
+    int e[CH_CHUNK], below[CH_CHUNK];
+#pragma unroll
+    for (int t = 0; t < CH_CHUNK; ++t) e[t] = (m0 + t < H) ? E[(int64_t)(m0 + t) * W + j] : CH_BIG;
+    int cb = Cb[(int64_t)q * W + j];
+#pragma unroll
+    for (int t = CH_CHUNK - 1; t >= 0; --t) {          // -3m + min_{k>=m} E(k) + 3k
+        cb = min(cb, e[t] + 3 * (m0 + t));
+        below[t] = cb;
+    }
+    int cf = Cf[(int64_t)q * W + j];
+#pragma unroll
+    for (int t = 0; t < CH_CHUNK; ++t) {              // 3m + min_{k<=m} E(k) - 3k
+        const int m = m0 + t;
+        if (m < H) {
+            const int64_t o = (int64_t)m * W + j;
+            cf = min(cf, e[t] - 3 * m);
+            const int d = min(D[o], min(3 * m + cf, -3 * m + below[t]));
+            D[o] = d >= CH_BIG / 2 ? INT32_MAX : d;
+        }
     }
 }
 
@@ -250,16 +292,17 @@ cudaError_t launch_chamfer(const uint8_t* mask, int H, int W, int mode, int32_t*
     const size_t smem = 2 * (size_t)(W + CH_ROWS) * sizeof(uint2);
     if ((e = traced("k_chamfer_rows", stream, [&] {
              if (W <= 8 * 1024)
-                 k_chamfer_rows<8><<<blocks, ((W + 255) / 256) * 32, smem, stream>>>(H, W, SW, sd, sa, D, E);
+                 k_chamfer_rows<8><<<blocks, ((W + 255) / 256) * 32, smem, stream>>>(H, W, SW, sd, sa, D, E, Tf,
+                                                                                     Tb);
              else
-                 k_chamfer_rows<16><<<blocks, ((W + 511) / 512) * 32, smem, stream>>>(H, W, SW, sd, sa, D, E);
+                 k_chamfer_rows<16><<<blocks, ((W + 511) / 512) * 32, smem, stream>>>(H, W, SW, sd, sa, D, E, Tf,
+                                                                                      Tb);
              return cudaGetLastError();
          })) != cudaSuccess)
         return e;
-    const dim3 grid((unsigned)((W + 127) / 128), (unsigned)nq);
     return traced("k_chamfer_cols", stream, [&] {
-        k_chamfer_cols_totals<<<grid, 128, 0, stream>>>(H, W, E, Tf, Tb);
-        k_chamfer_cols<<<grid, 128, 0, stream>>>(H, W, E, Tf, Tb, nq, D);
+        k_chamfer_cols_carry<<<(unsigned)((W + 31) / 32), 1024, 0, stream>>>(W, nq, Tf, Tb);
+        k_chamfer_cols<<<dim3((unsigned)((W + 127) / 128), (unsigned)nq), 128, 0, stream>>>(H, W, E, Tf, Tb, D);
         return cudaGetLastError();
     });
 }

@@ -51,7 +51,7 @@ __device__ __forceinline__ int staged_steps(uint2 c, int base, int r, int i)
     return d < 32768 ? d : CH_BIG;     // real distances stay below 32768 rows
 }
 
-// Column data {w, up | dn << 16} of column col of a sheared image's band b.
+// Column data {w, up | dn << 16} of column col of a sheared view's band b.
 __device__ __forceinline__ uint2 sheared_column(const ColScratch& s, int64_t SW, int b, int64_t col)
 {
     const uint32_t w = s.C[(int64_t)b * SW + col];

@@ -170,8 +170,9 @@ edt_status edt_batch(edt_plan *plan, const edt_job *jobs, int n,
  * and completes the ticket.  Each result is identical to a plain edt_feature
  * call on the same mask.  The budget is taken from the device when the
  * server is created (a memory pool of its own, grown to the budget less the
- * batch plans' scratch) and given back by edt_serve_destroy; EDT_ERR_CUDA if
- * the device cannot provide it. */
+ * batch plans' scratch) and given back by edt_serve_destroy; EDT_ERR_BUDGET
+ * when it exceeds the device's free memory or does not cover the plans,
+ * EDT_ERR_CUDA if the device still cannot provide it. */
 typedef struct edt_server edt_server;
 
 edt_status edt_serve_create(edt_server **server, size_t mem_budget_bytes,

@@ -277,6 +277,11 @@ extern "C" edt_status edt_serve_create(edt_server** out, size_t mem_budget_bytes
     int sms = 0;
     edt_status st = device_setup(&sms);
     if (st != EDT_OK) return st;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(EDT_ERR_CUDA, "cudaMemGetInfo failed");
+    if (mem_budget_bytes > free_b)
+        return fail(EDT_ERR_BUDGET, "budget of %zu bytes exceeds the %zu bytes free on the device", mem_budget_bytes,
+                    free_b);
     edt_server* s = new edt_server();
     cudaGetDevice(&s->device);
     s->sm_count = sms;

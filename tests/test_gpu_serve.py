@@ -98,3 +98,8 @@ def test_budget_and_bad_requests():
     lat, (D, F, dist) = _wait(srv, ok)
     assert torch.all(D == 2**31 - 1) and torch.all(F == -1)
     srv.close()
+    # a budget beyond the device's free memory is refused before any allocation
+    free, _ = torch.cuda.mem_get_info()
+    with pytest.raises(edt.EdtError) as e:
+        edt.Server(free + (1 << 30), n_streams=1)
+    assert e.value.status == 6

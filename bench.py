@@ -83,18 +83,39 @@ def kernel_sources_sha256(kernel: str) -> str:
     return h.hexdigest()
 
 
-def profile_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    that summary was taken on the current kernel sources (hash match)."""
+def profile_record(kernel: str):
+    """The committed ncu record of `kernel` (profiles/traffic.json) if it was
+    taken on the current kernel sources (hash match), else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             rec = json.load(fh)
         entry = rec.get(kernel)
         if not entry or entry.get("sources_sha256") != kernel_sources_sha256(kernel):
             return None
-        return entry.get("dram_bytes_per_launch_full_size")
+        return entry
     except Exception:
         return None
+
+
+def profile_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu record."""
+    entry = profile_record(kernel)
+    return None if entry is None else entry.get("dram_bytes_per_launch_full_size")
+
+
+def issue_roofline(kernel: str, launch_s: float, sm_mhz: float, sms: int):
+    """Instruction issue of `kernel`: the warp instructions one launch executes
+    (ncu record) over its CUDA-event launch time, against one warp
+    instruction per cycle on each of the 4 schedulers of every SM at the SM
+    clock sampled under load."""
+    entry = profile_record(kernel)
+    if entry is None or not entry.get("warp_instructions_per_launch") or not sm_mhz:
+        return None
+    achieved = entry["warp_instructions_per_launch"] / launch_s / 1e9
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_launch": entry["warp_instructions_per_launch"], "sms": sms,
+            "sm_mhz": sm_mhz}
 
 
 class ClockSampler:
@@ -692,7 +713,9 @@ def run_gpu(args, rank, world, local_rank):
                          "bytes_per_px": K2_BYTES_PER_PX, "px_per_launch": px_per_k2,
                          "peak_source": peak_kind,
                          "avg_launch_ms": k2_ms / max(k2_n, 1), "launches": k2_n,
-                         "k_colbits_avg_ms": k1_ms / max(k1_n, 1)},
+                         "k_colbits_avg_ms": k1_ms / max(k1_n, 1),
+                         "issue": issue_roofline("k_rows2d", k2_avg_s, clocks.get("sm_mhz") or 0,
+                                                 torch.cuda.get_device_properties(dev).multi_processor_count)},
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "four full steps (both transforms of the 8192x8192 discs "
                                        f"mask each), single-threaded C oracle, {cpu_s:.1f} s"},

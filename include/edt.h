@@ -38,6 +38,10 @@
  *   - Scratch memory: the plain calls draw their scratch from the device's
  *     stream-ordered memory pool (cudaMallocAsync on the given stream, freed on
  *     the same stream); batch plans and servers own theirs.
+ *   - Threads: the plain, pair, host-buffer, city-block and chamfer calls may
+ *     be made from several host threads at once (on separate streams, with
+ *     separate buffers); a plan is used from one thread at a time and
+ *     edt_feature2d_noalloc calls must be ordered by the caller (see there).
  */
 #ifndef LIBEDT_EDT_H
 #define LIBEDT_EDT_H

@@ -7,9 +7,10 @@
 // (i - g)^2 with g the nearest source row; here the same nearest row is
 // produced in a compact form that the row kernel expands on the fly:
 //   - one 32-bit word per (band of 32 rows, column) with the source bits,
-//     built by a warp from a 32 x 32 byte tile with 32 ballots (each lane
-//     loads 32 consecutive bytes of its own row; ballot t transposes byte t of
-//     all 32 rows into the word of column t);
+//     built by a warp from a 32 x 32 byte tile (each lane loads 32
+//     consecutive bytes of its own row and packs them into a row word; a
+//     five-stage shuffle butterfly transposes the 32 row words into the 32
+//     column words);
 //   - per band, the nearest source row above and below it inside its group of
 //     bands (32, or fewer for images too small to give 4096 warp units, never
 //     more than 32 groups to a column), from a forward and a backward scan
@@ -163,6 +164,26 @@ __device__ __forceinline__ uint32_t sheared_row_bits(const uint8_t* __restrict__
     return bits;
 }
 
+// 32 x 32 bit transpose across a warp: lane l holds row l (bit c = element
+// (l, c)); the result in lane c is column c (bit l = element (l, c)).  Five
+// butterfly stages: at distance j, lanes exchange words with lane l ^ j and
+// swap the j-bit blocks that lie on the wrong side of the diagonal.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
+{
+#define EDT_TRANSPOSE_STAGE(j, m)                                                          \
+    {                                                                                      \
+        const uint32_t y = __shfl_xor_sync(FULL, x, j);                                    \
+        x = (lane & (j)) ? ((x & ~(m)) | ((y >> (j)) & (m))) : ((x & (m)) | ((y << (j)) & ~(m))); \
+    }
+    EDT_TRANSPOSE_STAGE(16, 0x0000FFFFu)
+    EDT_TRANSPOSE_STAGE(8, 0x00FF00FFu)
+    EDT_TRANSPOSE_STAGE(4, 0x0F0F0F0Fu)
+    EDT_TRANSPOSE_STAGE(2, 0x33333333u)
+    EDT_TRANSPOSE_STAGE(1, 0x55555555u)
+#undef EDT_TRANSPOSE_STAGE
+    return x;
+}
+
 // Rows of band `band` that lie inside the image, as a bit mask.
 __device__ __forceinline__ uint32_t band_rows_mask(const ColGeom& g, int band)
 {
@@ -233,7 +254,11 @@ __device__ __forceinline__ void link_groups(const ColGeom& g, const ColScratch& 
 // view's column v at row r is the image's column v + r - (imgH - 1) (SHEAR
 // +1: the diagonals j - i = const become columns) or v - r (SHEAR -1: the
 // anti-diagonals); pixels outside the image are no sources.
-template <bool VEC, bool PAIR, int SHEAR = 0>
+//
+// BALLOT: transpose with 32 ballots instead of the shuffle butterfly (five
+// dependent shuffles); measured faster in the persistent batch kernel, where
+// each warp walks many small tiles one after the other.
+template <bool VEC, bool PAIR, int SHEAR = 0, bool BALLOT = false>
 __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g, int mode,
                              const ColScratch& s, const ColScratch& s1, int64_t tile, int G,
                              uint32_t (*cw)[32], uint32_t (*upS)[32], int imgH = 0, int64_t imgW = 0)
@@ -251,7 +276,7 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
                    ((reinterpret_cast<uintptr_t>(mask) & 15) == 0 ? 2 : 0);
     const uint8_t* mask_end = mask + (SHEAR == 0 ? (int64_t)g.rows * W : (int64_t)imgH * imgW);
 
-    // (1) source bits of 32 rows x 32 columns per band, transposed by ballots
+    // (1) source bits of 32 rows x 32 columns per band, transposed across the warp
     for (int bl = 0; bl < nbg; bl += 4) {
         uint32_t src[4];
 #pragma unroll
@@ -276,10 +301,14 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
         for (int u = 0; u < 4; ++u) {
             if (bl + u >= nbg) break;
             uint32_t mine = 0;
+            if (BALLOT) {
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                const uint32_t b = __ballot_sync(FULL, (src[u] >> t) & 1u);
-                if (lane == t) mine = b;
+                for (int t = 0; t < 32; ++t) {
+                    const uint32_t b = __ballot_sync(FULL, (src[u] >> t) & 1u);
+                    if (lane == t) mine = b;
+                }
+            } else {
+                mine = transpose32(src[u], lane);
             }
             cw[bl + u][lane] = mine;
             if (col < W) s.C[(int64_t)(b0 + bl + u) * W + col] = mine;
@@ -377,11 +406,11 @@ k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
         const ColScratch s = J.s;
         const int64_t local = gw - J.k1_first;
         if (J.vec)
-            colbits_warp<true, false>(J.mask, g, J.mode, s, s, local % g.ntiles, (int)(local / g.ntiles),
-                                      cw[warp], upS[warp]);
+            colbits_warp<true, false, 0, true>(J.mask, g, J.mode, s, s, local % g.ntiles,
+                                               (int)(local / g.ntiles), cw[warp], upS[warp]);
         else
-            colbits_warp<false, false>(J.mask, g, J.mode, s, s, local % g.ntiles, (int)(local / g.ntiles),
-                                       cw[warp], upS[warp]);
+            colbits_warp<false, false, 0, true>(J.mask, g, J.mode, s, s, local % g.ntiles,
+                                                (int)(local / g.ntiles), cw[warp], upS[warp]);
         __syncwarp();
     }
 }

@@ -87,6 +87,11 @@ static uint32_t xchg(uint32_t v, int src, const void* tag)
 }
 unsigned __shfl_sync(unsigned, unsigned v, int src) { return xchg(v, src, __builtin_return_address(0)); }
 int __shfl_sync(unsigned, int v, int src) { return (int)xchg((uint32_t)v, src, __builtin_return_address(0)); }
+unsigned __shfl_xor_sync(unsigned, unsigned v, int lanemask)
+{
+    const int lane = g_f[g_cur].tid & 31;
+    return xchg(v, lane ^ (lanemask & 31), __builtin_return_address(0));
+}
 int __shfl_up_sync(unsigned, int v, unsigned d)
 {
     const int lane = g_f[g_cur].tid & 31;

@@ -75,6 +75,7 @@ unsigned __shfl_sync(unsigned mask, unsigned v, int src);
 int __shfl_sync(unsigned mask, int v, int src);
 int __shfl_up_sync(unsigned mask, int v, unsigned d);
 int __shfl_down_sync(unsigned mask, int v, unsigned d);
+unsigned __shfl_xor_sync(unsigned mask, unsigned v, int lanemask);
 unsigned __ballot_sync(unsigned mask, int pred);
 unsigned __reduce_and_sync(unsigned mask, unsigned v);
 int __any_sync(unsigned mask, int pred);

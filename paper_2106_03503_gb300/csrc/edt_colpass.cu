@@ -338,16 +338,28 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
     if (lane == 0) s.cnt[tile] = 0u;  // ready for the next call
 }
 
+// Rows of a warp's two shared scratch tiles: the bands of a group, or the
+// groups of a column when there are more of those.
+__host__ __device__ inline int colbits_tile_rows(const ColGeom& g)
+{
+    return (1 << g.gs) > g.nG ? (1 << g.gs) : g.nG;
+}
+
+// Shared scratch per warp: two tiles of colbits_tile_rows(g) x 32 words
+// (dynamic, so that small groups leave room for more resident blocks).
 template <bool VEC, bool PAIR>
 __global__ void __launch_bounds__(K1_WARPS * 32)
 k_colbits(const uint8_t* __restrict__ mask, ColGeom g, int mode, ColScratch s, ColScratch s1)
 {
-    __shared__ uint32_t cw[K1_WARPS][32][32];   // [warp][band][column]
-    __shared__ uint32_t upS[K1_WARPS][32][32];  // forward-scan results
+    extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
+    const int R = colbits_tile_rows(g);
+    uint32_t (*cw)[32] =
+        reinterpret_cast<uint32_t (*)[32]>(reinterpret_cast<uint32_t*>(smem) + (size_t)warp * 2 * R * 32);  // [band][column]
+    uint32_t (*upS)[32] = cw + R;                                                                   // forward scans
     const int64_t gw = (int64_t)blockIdx.x * K1_WARPS + warp;
     if (gw >= g.ntiles * (int64_t)g.nG) return;  // whole warp; no block sync below
-    colbits_warp<VEC, PAIR>(mask, g, mode, s, s1, gw % g.ntiles, (int)(gw / g.ntiles), cw[warp], upS[warp]);
+    colbits_warp<VEC, PAIR>(mask, g, mode, s, s1, gw % g.ntiles, (int)(gw / g.ntiles), cw, upS);
 }
 
 // Column pass over a sheared view (see colbits_warp) of an imgH x imgW mask;
@@ -436,11 +448,12 @@ cudaError_t launch_colbits(const uint8_t* mask, const ColGeom& g, int mode,
 {
     const int64_t warps = g.ntiles * (int64_t)g.nG;
     const int64_t blocks = (warps + K1_WARPS - 1) / K1_WARPS;
+    const size_t smem = (size_t)K1_WARPS * 2 * colbits_tile_rows(g) * 32 * 4;
     const bool vec = (g.cols % 16 == 0) && ((reinterpret_cast<uintptr_t>(mask) & 15) == 0);
     if (vec)
-        k_colbits<true, false><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s, s);
+        k_colbits<true, false><<<(unsigned)blocks, K1_WARPS * 32, smem, stream>>>(mask, g, mode, s, s);
     else
-        k_colbits<false, false><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, mode, s, s);
+        k_colbits<false, false><<<(unsigned)blocks, K1_WARPS * 32, smem, stream>>>(mask, g, mode, s, s);
     return cudaGetLastError();
 }
 
@@ -451,11 +464,12 @@ cudaError_t launch_colbits_pair(const uint8_t* mask, const ColGeom& g, const Col
 {
     const int64_t warps = g.ntiles * (int64_t)g.nG;
     const int64_t blocks = (warps + K1_WARPS - 1) / K1_WARPS;
+    const size_t smem = (size_t)K1_WARPS * 2 * colbits_tile_rows(g) * 32 * 4;
     const bool vec = (g.cols % 16 == 0) && ((reinterpret_cast<uintptr_t>(mask) & 15) == 0);
     if (vec)
-        k_colbits<true, true><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, 0, s, s1);
+        k_colbits<true, true><<<(unsigned)blocks, K1_WARPS * 32, smem, stream>>>(mask, g, 0, s, s1);
     else
-        k_colbits<false, true><<<(unsigned)blocks, K1_WARPS * 32, 0, stream>>>(mask, g, 0, s, s1);
+        k_colbits<false, true><<<(unsigned)blocks, K1_WARPS * 32, smem, stream>>>(mask, g, 0, s, s1);
     return cudaGetLastError();
 }
 

@@ -18,8 +18,10 @@
 //   - per group, the nearest source above and below it over the whole column,
 //     computed by whichever warp of a 32-column tile finishes last (an arrival
 //     counter per tile; no warp ever waits for another).
-// A mask byte is read exactly once, with 16-byte loads where the row layout
-// allows it.
+// Where rows start on 16-byte boundaries (width a multiple of 16) every mask
+// byte is loaded once, with 16-byte loads; otherwise a 32-byte row window is
+// read as the aligned chunks or words that cover it, so the few bytes shared
+// by two tiles' windows are loaded by both.
 #include "edt_engine.cuh"
 #include "edt_internal.h"
 

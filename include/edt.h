@@ -223,6 +223,32 @@ edt_status edt_feature2d_noalloc(const uint8_t *mask, int H, int W, int mode,
                                  int32_t *D, int32_t *F, float *dist,
                                  edt_stream_t stream);
 
+/* Autotuning of the band geometry.  The envelope passes give each band of
+ * 32 lines (rows for 2-D, y and x lines for 3-D) several warps, each taking
+ * one segment of the lines, and merge the segments' envelopes; the number of
+ * warps per band trades per-warp work against merge depth and resident
+ * blocks.  edt_autotune times the candidates (2-D rows: 16, 8, 4 warps; 3-D
+ * y pass: 8, 4, 16, 32, then x pass: 32, 16, 8) on `mask` (DEVICE, the given
+ * shape and mode) and keeps the fastest for the shape's class -- the
+ * rounded-up log2 of each side -- in a process-wide table that every later
+ * call of that class uses (plain, pair and host-buffer calls; batches keep
+ * their own rule).  Results do not depend on the choice: D and F are the same
+ * bits for every candidate.  Synchronous; device scratch from the stream's
+ * pool.  Without tuning, the built-in rule applies (16, 8, 32). */
+edt_status edt_autotune(const uint8_t *mask, int ndim, const int *shape,
+                        int mode, edt_stream_t stream);
+/* The tuned warps per band of a shape's class: warps[0] = 2-D rows,
+ * warps[1] = 3-D y pass, warps[2] = 3-D x pass; 0 = the built-in rule.
+ * Host-only (no device needed). */
+edt_status edt_tune_get(int ndim, const int *shape, int *warps);
+/* Write the table to a text file / merge a file into the table (lines of
+ * "ndim log2(side0) log2(side1) log2(side2) rows2d ypass xpass", '#' starts
+ * a comment; warp counts are powers of two up to 16, 32, 32, or 0).
+ * Host-only; EDT_ERR_INVALID for unreadable or malformed files (the table is
+ * then unchanged). */
+edt_status edt_tune_save(const char *path);
+edt_status edt_tune_load(const char *path);
+
 /* Message of the last failure on the calling thread ("" when none). */
 const char *edt_last_error(void);
 

@@ -226,7 +226,9 @@ cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
     // nearest-z entries), so more blocks fit per SM and the merge tree is
     // shallower (measured on 512^3: 1.60 ms with 8, 1.88 ms with 16 warps)
     int lg, NW;
-    pick_band(H, ypass_smem, 8, lg, NW);
+    const int shape3[3] = {Dz, H, W};
+    const Tuning tu = tuning_lookup(3, shape3);
+    pick_band(H, ypass_smem, tu.ypass_nw > 0 ? tu.ypass_nw : 8, lg, NW);
     const int xtiles = (W + 31) / 32;
     const unsigned blocks = (unsigned)((int64_t)Dz * xtiles);
     k_ypass3d<<<blocks, NW * 32, ypass_smem(H, lg, NW), stream>>>(H, W, s, lg, NW, P);
@@ -237,7 +239,9 @@ cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,
                            int32_t* F, float* dist, cudaStream_t stream)
 {
     int lg, NW;
-    pick_band(W, xpass_smem, 32, lg, NW);
+    const int shape3[3] = {Dz, H, W};
+    const Tuning tu = tuning_lookup(3, shape3);
+    pick_band(W, xpass_smem, tu.xpass_nw > 0 ? tu.xpass_nw : 32, lg, NW);
     const int64_t nrows = (int64_t)Dz * H;
     const unsigned blocks = (unsigned)((nrows + 31) / 32);
     k_xpass3d<<<blocks, NW * 32, xpass_smem(W, lg, NW), stream>>>(Dz, H, W, lg, NW, P, D, F, dist);

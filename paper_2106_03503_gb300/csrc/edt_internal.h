@@ -133,6 +133,18 @@ cudaError_t traced(const char* kernel, cudaStream_t stream, F&& launch)
     return e;
 }
 
+// Tuned geometry (edt_autotune) per shape class: the upper bound on warps per
+// band -- hence the segment length along the lines -- of the 2-D row pass and
+// of the 3-D y and x passes; 0 = the built-in rule (16, 8, 32).  The class of
+// a shape is the rounded-up log2 of each side.
+struct Tuning {
+    int rows2d_nw = 0;
+    int ypass_nw = 0;
+    int xpass_nw = 0;
+};
+Tuning tuning_lookup(int ndim, const int* shape);
+void tuning_store(int ndim, const int* shape, const Tuning& t);
+
 cudaError_t set_2d_attributes();
 cudaError_t set_chamfer_attributes();
 cudaError_t set_3d_attributes();

@@ -241,7 +241,9 @@ static cudaError_t launch_rows(int H, int W, const RowJob& J0, const RowJob* J1,
         if (jobs[k]->F) tma = tma && make_row_map(&m[3 * k + 1], jobs[k]->F, false, H, W);
         if (jobs[k]->dist) tma = tma && make_row_map(&m[3 * k + 2], jobs[k]->dist, true, H, W);
     }
-    int max_nw = 16, lg = 0, NW = 0;
+    const int shape2[2] = {H, W};
+    const Tuning tu = tuning_lookup(2, shape2);
+    int max_nw = tu.rows2d_nw > 0 ? tu.rows2d_nw : 16, lg = 0, NW = 0;
     size_t smem = 0;
     for (; max_nw >= 1; max_nw >>= 1) {
         lg = band_seg_log2(W, max_nw);

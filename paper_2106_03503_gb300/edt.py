@@ -64,6 +64,14 @@ _lib.edt_trace_enable.restype = ctypes.c_int
 _lib.edt_trace_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int64)]
 _lib.edt_trace_read.restype = ctypes.c_int
+_lib.edt_autotune.argtypes = [_vp, ctypes.c_int, _i32p, ctypes.c_int, _vp]
+_lib.edt_autotune.restype = ctypes.c_int
+_lib.edt_tune_get.argtypes = [ctypes.c_int, _i32p, _i32p]
+_lib.edt_tune_get.restype = ctypes.c_int
+_lib.edt_tune_save.argtypes = [ctypes.c_char_p]
+_lib.edt_tune_save.restype = ctypes.c_int
+_lib.edt_tune_load.argtypes = [ctypes.c_char_p]
+_lib.edt_tune_load.restype = ctypes.c_int
 _lib.edt_last_error.restype = ctypes.c_char_p
 _lib.edt_version.restype = ctypes.c_char_p
 for _name in ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_host", "edt_feature_pair"):
@@ -74,7 +82,34 @@ EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_pair", "edt_featu
            "edt_plan_create",
            "edt_plan_destroy", "edt_batch", "edt_serve_create", "edt_serve_submit",
            "edt_serve_poll", "edt_serve_destroy", "edt_trace_enable", "edt_trace_read",
+           "edt_autotune", "edt_tune_get", "edt_tune_save", "edt_tune_load",
            "edt_last_error", "edt_version")
+
+
+def tune_get(shape):
+    """Tuned warps per band of a shape's class: {"rows2d": .., "ypass": ..,
+    "xpass": ..}; 0 = the built-in rule."""
+    w = (ctypes.c_int * 3)()
+    _check(_lib.edt_tune_get(len(shape), _shape_arr(shape), w))
+    return {"rows2d": w[0], "ypass": w[1], "xpass": w[2]}
+
+
+def autotune(mask, mode: int = TO_OBJECT, stream=None):
+    """Time the band-geometry candidates on this CUDA mask (edt_autotune) and
+    keep the fastest for its shape class; returns tune_get(shape)."""
+    m = _mask_arg(mask)
+    _check(_lib.edt_autotune(_ptr(m), m.dim(), _shape_arr(m.shape), int(mode), _stream_handle(stream)))
+    return tune_get(tuple(m.shape))
+
+
+def tune_save(path: str):
+    """Write the tuning table to a text file (edt_tune_save)."""
+    _check(_lib.edt_tune_save(os.fsencode(path)))
+
+
+def tune_load(path: str):
+    """Merge a tuning file into the table (edt_tune_load)."""
+    _check(_lib.edt_tune_load(os.fsencode(path)))
 
 
 def trace_enable(on: bool = True):

@@ -80,3 +80,35 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
 def test_version_string(lib):
     lib.edt_version.restype = ctypes.c_char_p
     assert b"libedt" in lib.edt_version()
+
+
+def test_tuning_table_load_get_save(lib, tmp_path):
+    """The autotuner's table on the host: a file merges into it, queries map
+    a shape to its class (rounded-up log2 of each side), a save writes it back,
+    malformed or out-of-range files are refused and leave it unchanged."""
+    i3 = ctypes.c_int * 3
+    lib.edt_tune_get.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.edt_tune_load.argtypes = [ctypes.c_char_p]
+    lib.edt_tune_save.argtypes = [ctypes.c_char_p]
+    good = tmp_path / "tune.txt"
+    good.write_text("# comment\n2 10 13 0 8 0 0\n3 9 9 9 0 4 16\n")
+    assert lib.edt_tune_load(str(good).encode()) == 0
+    w = i3()
+    assert lib.edt_tune_get(2, (ctypes.c_int * 2)(1000, 8192), w) == 0 and list(w) == [8, 0, 0]
+    assert lib.edt_tune_get(2, (ctypes.c_int * 2)(513, 4097), w) == 0 and list(w) == [8, 0, 0]
+    assert lib.edt_tune_get(2, (ctypes.c_int * 2)(512, 8192), w) == 0 and list(w) == [0, 0, 0]
+    assert lib.edt_tune_get(3, (ctypes.c_int * 3)(512, 300, 257), w) == 0 and list(w) == [0, 4, 16]
+    for bad in ("2 10 13\n", "4 1 1 1 0 0 0\n", "2 10 13 0 12 0 0\n", "3 9 9 9 0 64 0\n"):
+        f = tmp_path / "bad.txt"
+        f.write_text(bad)
+        assert lib.edt_tune_load(str(f).encode()) == 1, bad
+    assert lib.edt_tune_load(str(tmp_path / "missing.txt").encode()) == 1
+    assert lib.edt_tune_get(3, (ctypes.c_int * 3)(512, 300, 257), w) == 0 and list(w) == [0, 4, 16]
+    out = tmp_path / "saved.txt"
+    assert lib.edt_tune_save(str(out).encode()) == 0
+    lines = [ln.split() for ln in out.read_text().splitlines() if ln and not ln.startswith("#")]
+    assert ["2", "10", "13", "0", "8", "0", "0"] in lines and ["3", "9", "9", "9", "0", "4", "16"] in lines
+    assert lib.edt_tune_get(4, (ctypes.c_int * 3)(1, 1, 1), w) == 1
+    reset = tmp_path / "reset.txt"          # the table is process-wide: leave the rules in force
+    reset.write_text("2 10 13 0 0 0 0\n3 9 9 9 0 0 0\n")
+    assert lib.edt_tune_load(str(reset).encode()) == 0

@@ -1,9 +1,11 @@
 // Driver of the host emulation of libedt's kernels (test infrastructure):
-// runs the 2-D column and row kernels (single transforms and the fused pair)
-// and the 3-D passes on seeded random masks and compares the result with the
+// runs the 2-D column and row kernels (single transforms and the fused pair),
+// the 3-D passes, the city-block and chamfer passes and the persistent batch
+// kernels on seeded random masks and compares the result with the
 // CPU oracle: D exactly, F a source at squared distance D.
 //   emu 2d PART NPARTS   2-D cases whose index is PART modulo NPARTS
 //   emu 3d               3-D cases
+//   emu batch            batches through the persistent kernels
 #include "shim.h"
 #include "src/edt_internal.h"
 extern "C" {
@@ -116,6 +118,74 @@ static int run3d(int Dz, int H, int W, double p, int mode)
     return bad;
 }
 
+// A batch through the two persistent kernels, laid out as edt_batch lays it
+// out: jobs sorted widest first, per-job scratch with the batch geometry
+// (32-band groups), unit ranges by prefix sums, one work counter.
+static int run_batch(int njobs, int blocks)
+{
+    struct Job {
+        std::vector<uint8_t> mask;
+        int H, W, mode;
+        int32_t *D, *F;
+        std::vector<unsigned char> scratch;
+    };
+    std::vector<Job> js(njobs);
+    const double ps[] = {0.0, 0.001, 0.02, 0.3, 1.0};
+    for (int k = 0; k < njobs; ++k) {
+        Job& j = js[k];
+        j.H = 1 + (int)(urand() * 300);
+        j.W = 1 + (int)(urand() * (k % 3 == 0 ? 2048 : 300));
+        j.mode = k & 1;
+        const double p = ps[k % 5];
+        j.mask.resize((size_t)j.H * j.W);
+        for (auto& m : j.mask) m = urand() < p;
+        j.D = alloc_words((size_t)j.H * j.W);
+        j.F = alloc_words((size_t)j.H * j.W);
+    }
+    std::vector<int> order(njobs);
+    for (int k = 0; k < njobs; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return js[a].W > js[c].W; });
+    std::vector<unsigned char> table(sizeof(BatchHeader) + (size_t)njobs * sizeof(BatchJob) + 256);
+    auto* hdr = reinterpret_cast<BatchHeader*>(((uintptr_t)table.data() + 255) & ~uintptr_t(255));
+    auto* tab = reinterpret_cast<BatchJob*>(hdr + 1);
+    int64_t k1 = 0, k2 = 0;
+    for (int t = 0; t < njobs; ++t) {
+        Job& j = js[order[t]];
+        BatchJob& J = tab[t];
+        memset(&J, 0, sizeof(J));
+        J.mask = j.mask.data();
+        J.D = j.D;
+        J.F = j.F;
+        J.dist = nullptr;
+        J.g = col_geom(j.H, j.W, true);
+        J.mode = j.mode;
+        J.vec = (j.W % 16 == 0) && ((reinterpret_cast<uintptr_t>(j.mask.data()) & 15) == 0);
+        j.scratch.assign(col_scratch_bytes(J.g) + 256, 0);
+        J.s = col_scratch_carve((void*)(((uintptr_t)j.scratch.data() + 255) & ~uintptr_t(255)), J.g);
+        batch_row_geometry(j.W, J.lg, J.NW, J.groups);
+        J.k1_first = k1;
+        J.k2_first = k2;
+        k1 += J.g.ntiles * (int64_t)J.g.nG;
+        k2 += (J.g.nb + J.groups - 1) / J.groups;
+    }
+    hdr->njobs = njobs;
+    hdr->pad0 = 0;
+    hdr->k1_total = k1;
+    hdr->k2_total = k2;
+    unsigned work = 0;
+    launch_batch_colbits(hdr, tab, blocks, nullptr);
+    launch_batch_rows2d(hdr, tab, &work, blocks, nullptr);
+    int bad = 0;
+    for (Job& j : js) {
+        std::vector<int32_t> Do((size_t)j.H * j.W), Fo((size_t)j.H * j.W);
+        oracle_edt2d(j.mask.data(), j.H, j.W, j.mode, Do.data(), Fo.data());
+        bad += check_features(j.mask, j.H, j.W, j.mode, j.D, j.F, Do);
+        free(j.D);
+        free(j.F);
+    }
+    return bad;
+}
+
 static int run_cityblock(int H, int W, double p, int mode, int align_off)
 {
     std::vector<uint8_t> mask((size_t)H * W);
@@ -186,6 +256,16 @@ int main(int argc, char** argv)
                 bad += run_cityblock(sh[0], sh[1], p, c & 1, c % 3 == 0 ? 4 : 0);
             }
         printf("cityblock cases %d bad %d\n", run, bad);
+        return bad != 0;
+    }
+    if (argc > 1 && !strcmp(argv[1], "batch")) {
+        int bad = 0, cases = 0;
+        for (int njobs : {1, 5, 17})
+            for (int blocks : {1, 3}) {
+                bad += run_batch(njobs, blocks);
+                ++cases;
+            }
+        printf("batch cases %d bad %d\n", cases, bad);
         return bad != 0;
     }
     if (argc > 1 && !strcmp(argv[1], "3d")) {

@@ -71,6 +71,10 @@ def test_kernels_3d_match_oracle(emu):
     _run_all([[emu, "3d"]])
 
 
+def test_batch_kernels_match_oracle(emu):
+    _run_all([[emu, "batch"]])
+
+
 def test_cityblock_kernel_matches_oracle(emu):
     n = max(1, min(8, os.cpu_count() or 1))
     _run_all([[emu, "cityblock", str(k), str(n)] for k in range(n)])

@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` use this package; the CUDA library and its Python
 binding never import it.  The arithmetic lives in ``edt_oracle.c`` (plain,
 single-threaded C following Section 3 of T. Strutz, "The Distance Transform
-and its Computation"); this module only compiles it with gcc and marshals
+and its Computation", written from its definitions and equations); this
+module only compiles it with gcc and marshals
 numpy arrays through ctypes.
 
 Conventions (shared by value, not by code, with the CUDA library):
@@ -152,15 +153,16 @@ def column_pass(mask, mode: int = TO_OBJECT, down_only: bool = False):
 
 
 def envelope_state(f, maxd: int):
-    """First scan of Sec. 3.3.1 on one line: (ks, js) as 0-based int64 arrays."""
+    """Envelope list of Sec. 3.3.1 on one line: (sites, starts) as 0-based
+    int64 arrays; starts has one more entry, the line length."""
     lib = _load()
     fv = np.ascontiguousarray(f, dtype=np.int64)
     n = fv.shape[0]
-    ks = np.empty(n + 1, dtype=np.int64)
-    js = np.empty(n + 2, dtype=np.int64)
+    site = np.empty(n + 1, dtype=np.int64)
+    start = np.empty(n + 1, dtype=np.int64)
     cnt = lib.oracle_envelope_state(_ptr(fv, ctypes.c_int64), n, int(maxd),
-                                    _ptr(ks, ctypes.c_int64), _ptr(js, ctypes.c_int64))
-    return ks[:cnt].copy(), js[:cnt + 1].copy()
+                                    _ptr(site, ctypes.c_int64), _ptr(start, ctypes.c_int64))
+    return site[:cnt].copy(), start[:cnt + 1].copy()
 
 
 def sqrt_f32(D) -> np.ndarray:

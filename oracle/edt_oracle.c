@@ -1,7 +1,10 @@
 /*
  * Oracle for the exact Euclidean distance transform (EEDT) and its feature
  * (nearest source pixel) map, after T. Strutz, "The Distance Transform and its
- * Computation -- An Introduction", Section 3.
+ * Computation -- An Introduction", Section 3.  It is written from the
+ * definitions the paper gives (the vertical distance to the nearest source of
+ * a column, Sec. 3.1; the parabolas of Eq. (5) and their intersections,
+ * Eq. (6), Sec. 3.3.1), not from the paper's program listings.
  *
  * TEST INFRASTRUCTURE ONLY.  This file is plain, slow, single-threaded C that
  * exists to check the CUDA path.  Only the tests, the smoke check and the CPU
@@ -20,16 +23,19 @@
  *   - only pixels inside the image count; there is no virtual border.
  *   - "infinity" is any value >= max_dist, where max_dist is one more than the
  *     largest squared distance inside the image (Sec. 3.1 asks for a value
- *     larger than (M-1)^2 + (L-1)^2).  Values produced from an infinite input
- *     are clamped back to max_dist, with feature -1.
+ *     larger than (M-1)^2 + (L-1)^2).  The envelope only takes finite values
+ *     as parabola vertices, so every finite result is a real distance; there
+ *     is no dummy first parabola.
  *   - an image without any source pixel yields D = INT32_MAX, F = -1
- *     everywhere (the listings would return max_dist + (j-1)^2 there).
+ *     everywhere (the paper's algorithm would return a value derived from the
+ *     initial infinity there).
  *   - the intersection of Eq. (6) is rounded up with exact integer ceiling
  *     division; no floating point is used.
- *   - ties: the column scans keep the upper source (strict comparisons), the
- *     envelope hands an integer intersection to the right-hand parabola (the
- *     "j <= js" pop of the fast algorithm); a returned feature is one valid
- *     nearest source, not the only one.
+ *   - ties: the column distances keep the upper source (the scans of Sec. 3.1
+ *     replace a value only by a strictly smaller one), the envelope hands an
+ *     integer intersection to the right-hand parabola (Fig. 21: the ties "2/5"
+ *     and "5/8" go to 5 and 8); a returned feature is one valid nearest
+ *     source, not the only one.
  *   - 3-D: the paper only says that the dimensions are processed separately
  *     (Sec. 3.1); here the scan runs along z, then the envelope along y, then
  *     along x.
@@ -54,38 +60,42 @@ int64_t oracle_max_dist(int ndim, const int *shape)
     return s;
 }
 
-/* Sec. 3.1, Fig. 19 and Fig. 18(b): the column scans of Listing 7 ("Simple
- * EEDT algorithm").  A downward scan then an upward scan
- * propagate squared distances along one line of n values spaced by `stride`;
- * the step to the next square is the odd number dist_step, which grows by 2
- * per propagated pixel and falls back to 1 where nothing is propagated, since
- * (x+1)^2 - x^2 = 2x + 1.  The feature index travels with the value. */
-static void column_scan(int64_t *d, int32_t *feat, long n, long stride,
-                        int down_only)
+/* Sec. 3.1, Fig. 18(b) and Fig. 19: the squared vertical distance of a pixel
+ * is the squared row difference to the nearest source pixel of its own column
+ * (Eq. (5) restricted to one column).  Along one line of n values spaced by
+ * `stride`, where a source holds d = 0, one sweep downwards records for every
+ * position the nearest source at or above it, one sweep upwards the nearest
+ * at or below it; the nearer of the two is kept, the upper one when both are
+ * equally far (the scans of Sec. 3.1 replace a value only by a strictly
+ * smaller one, so the value that arrived from above first stays).  With
+ * down_only set, only sources at or above count (the state of Fig. 19).
+ * Positions without a source in reach keep their value (infinity).  The
+ * feature index of the chosen source travels with the distance.  `above` is
+ * scratch space for n positions. */
+static void column_nearest(int64_t *d, int32_t *feat, long n, long stride,
+                           int down_only, long *above)
 {
-    int64_t dist_step = 1;
-    for (long i = 1; i < n; ++i) {
-        int64_t cand = d[(i - 1) * stride] + dist_step;
-        if (d[i * stride] > cand) {
-            d[i * stride] = cand;
-            feat[i * stride] = feat[(i - 1) * stride];
-            dist_step += 2;
-        } else {
-            dist_step = 1;
-        }
+    long last = -1;
+    for (long i = 0; i < n; ++i) {
+        if (d[i * stride] == 0)
+            last = i;
+        above[i] = last;
     }
-    if (down_only)
-        return;
-    dist_step = 1;
-    for (long i = n - 2; i >= 0; --i) {
-        int64_t cand = d[(i + 1) * stride] + dist_step;
-        if (d[i * stride] > cand) {
-            d[i * stride] = cand;
-            feat[i * stride] = feat[(i + 1) * stride];
-            dist_step += 2;
-        } else {
-            dist_step = 1;
-        }
+    long next = -1;
+    for (long i = n - 1; i >= 0; --i) {
+        if (d[i * stride] == 0)
+            next = i;
+        long up = above[i];
+        long dn = down_only ? -1 : next;
+        long g;
+        if (up < 0 && dn < 0)
+            continue;
+        if (dn < 0 || (up >= 0 && i - up <= dn - i))
+            g = up;
+        else
+            g = dn;
+        d[i * stride] = (int64_t)(i - g) * (int64_t)(i - g);
+        feat[i * stride] = feat[g * stride];
     }
 }
 
@@ -100,76 +110,73 @@ static int64_t ceil_div(int64_t num, int64_t den)
     return q;
 }
 
-/* Eq. (6): the intersection j_s of the parabolas of Eq. (5) with vertices at
- * k < l, rounded up to the first integer position where l is not worse. */
-static int64_t intersection_ceil(const int64_t *f, long stride, int64_t k,
-                                 int64_t l)
+/* Eq. (6) for the parabolas of Eq. (5) with vertices k < m: m is not worse
+ * than k at position j exactly when
+ *     2 j (m - k) >= f(m) - f(k) + m^2 - k^2,
+ * so the first integer position where m is not worse is the ceiling of the
+ * right-hand side over 2 (m - k).  At an integer intersection the two are
+ * equal and m, the right-hand parabola, is taken. */
+static int64_t first_not_worse(const int64_t *f, int64_t k, int64_t m)
 {
-    int64_t num = f[l * stride] - f[k * stride] - k * k + l * l;
-    return ceil_div(num, 2 * (l - k));
+    return ceil_div(f[m] - f[k] + m * m - k * k, 2 * (m - k));
 }
 
-/* Sec. 3.3.1 (Meijster et al.; Listing 9, "Fast algorithm for EEDT"): the
- * lower envelope of the parabolas D_k(j) = f(k) + (j - k)^2 of Eq. (5) along
- * one line of n values spaced by `stride`.
- *
- * First scan: walk the line left to right; each finite f(m) is a candidate
- * contributor.  Its intersection with the last stored contributor is computed
- * with Eq. (6); while it does not lie beyond that contributor's start, the
- * stored contributor is hidden and dropped.  A candidate whose intersection
- * lies beyond the end of the line is not stored.  ks[] holds the stored
- * contributors, js[] their first columns (0-based; js[0] is the stopping
- * point -max_dist during the scan and is closed to 0 afterwards, js[cnt] = n).
- * The first contributor is column 0, possibly a dummy with f = infinity,
- * exactly as in the paper.
- *
- * Returns the number of stored contributors cnt (ks[0..cnt-1], js[0..cnt]). */
-static long envelope_scan(const int64_t *f, long n, long stride,
-                          int64_t max_dist, int64_t *ks, int64_t *js)
+/* Sec. 3.3.1, Eq. (5) and Eq. (6): along one line f[0..n-1] (values >=
+ * max_dist are infinite), position j receives the minimum over k of
+ * f(k) + (j - k)^2, taken at a minimising k that moves right as j grows.
+ * The positions k that give the minimum somewhere form a list ordered by k,
+ * each with the first position it takes, `start`; it keeps the positions up
+ * to the next start.  Visiting the finite positions m from left to right:
+ * while m is not worse than the last listed k already at k's start, k gives
+ * the minimum nowhere and leaves the list; then m is listed from the first
+ * position where it is not worse than the last remaining entry (position 0
+ * when none remains), unless that position lies beyond the line.  Returns the
+ * number of entries; site[] and start[] hold them, start[cnt] = n. */
+static long lower_envelope(const int64_t *f, long n, int64_t max_dist,
+                           int64_t *site, int64_t *start)
 {
-    long idx = 0;
-    js[0] = -max_dist;
-    ks[0] = 0;
-    for (long m = 1; m < n; ++m) {
-        if (f[m * stride] >= max_dist)
+    long cnt = 0;
+    for (long m = 0; m < n; ++m) {
+        if (f[m] >= max_dist)
             continue;
-        int64_t k = ks[idx];
-        int64_t j = intersection_ceil(f, stride, k, m);
-        while (j <= js[idx]) {
-            idx -= 1;
-            k = ks[idx];
-            j = intersection_ceil(f, stride, k, m);
+        int64_t s = 0;
+        while (cnt > 0) {
+            s = first_not_worse(f, site[cnt - 1], m);
+            if (s > start[cnt - 1])
+                break;
+            cnt -= 1;
+            s = 0;
         }
-        if (j <= n - 1) {
-            idx += 1;
-            js[idx] = j > 0 ? j : 0;
-            ks[idx] = m;
-        }
+        if (s > n - 1)
+            continue;
+        site[cnt] = m;
+        start[cnt] = s;
+        cnt += 1;
     }
-    js[0] = 0;
-    js[idx + 1] = n;
-    return idx + 1;
+    start[cnt] = n;
+    return cnt;
 }
 
-/* Second scan of Sec. 3.3.1: every position j in [js[p], js[p+1]) takes its
- * value from contributor ks[p] through Eq. (5), and its feature with it.
- * Values reached only from an infinite input are clamped to max_dist. */
-static void envelope_fill(const int64_t *f, const int32_t *feat_in,
-                          long stride, int64_t max_dist, const int64_t *ks,
-                          const int64_t *js, long cnt, int64_t *out,
+/* Eq. (5) evaluated from the list: positions start[p] .. start[p+1]-1 take
+ * f(site[p]) + (j - site[p])^2 and that site's feature.  A line without any
+ * finite value stays infinite, feature -1. */
+static void envelope_fill(const int64_t *f, const int32_t *feat_in, long n,
+                          int64_t max_dist, const int64_t *site,
+                          const int64_t *start, long cnt, int64_t *out,
                           int32_t *feat_out)
 {
+    if (cnt == 0) {
+        for (long j = 0; j < n; ++j) {
+            out[j] = max_dist;
+            feat_out[j] = -1;
+        }
+        return;
+    }
     for (long p = 0; p < cnt; ++p) {
-        int64_t k = ks[p];
-        for (int64_t j = js[p]; j < js[p + 1]; ++j) {
-            int64_t v = f[k * stride] + (j - k) * (j - k);
-            if (f[k * stride] >= max_dist || v >= max_dist) {
-                out[j * stride] = max_dist;
-                feat_out[j * stride] = -1;
-            } else {
-                out[j * stride] = v;
-                feat_out[j * stride] = feat_in[k * stride];
-            }
+        int64_t k = site[p];
+        for (int64_t j = start[p]; j < start[p + 1]; ++j) {
+            out[j] = f[k] + (j - k) * (j - k);
+            feat_out[j] = feat_in[k];
         }
     }
 }
@@ -202,25 +209,50 @@ static void finish(const int64_t *d, const int32_t *feat, long n,
     }
 }
 
-/* Strided envelope pass: gather the line, run the two scans, scatter back. */
+/* Working space of the line passes (one line at a time). */
+typedef struct {
+    int64_t *fv, *out, *site, *start;
+    int32_t *featv, *featout;
+    long *above;
+} line_work;
+
+static int work_alloc(line_work *w, long line)
+{
+    size_t n = (size_t)(line > 0 ? line : 1);
+    w->fv = malloc(sizeof(int64_t) * n);
+    w->out = malloc(sizeof(int64_t) * n);
+    w->site = malloc(sizeof(int64_t) * (n + 1));
+    w->start = malloc(sizeof(int64_t) * (n + 1));
+    w->featv = malloc(sizeof(int32_t) * n);
+    w->featout = malloc(sizeof(int32_t) * n);
+    w->above = malloc(sizeof(long) * n);
+    return (w->fv && w->out && w->site && w->start && w->featv && w->featout && w->above) ? 0 : -1;
+}
+
+static void work_free(line_work *w)
+{
+    free(w->fv); free(w->out); free(w->site); free(w->start);
+    free(w->featv); free(w->featout); free(w->above);
+}
+
+/* One envelope pass along a strided line: gather, envelope, fill, scatter. */
 static void envelope_pass(int64_t *d, int32_t *feat, long n, long stride,
-                          int64_t max_dist, int64_t *fv, int32_t *featv,
-                          int64_t *out, int32_t *featout, int64_t *ks,
-                          int64_t *js)
+                          int64_t max_dist, line_work *w)
 {
     for (long j = 0; j < n; ++j) {
-        fv[j] = d[j * stride];
-        featv[j] = feat[j * stride];
+        w->fv[j] = d[j * stride];
+        w->featv[j] = feat[j * stride];
     }
-    long cnt = envelope_scan(fv, n, 1, max_dist, ks, js);
-    envelope_fill(fv, featv, 1, max_dist, ks, js, cnt, out, featout);
+    long cnt = lower_envelope(w->fv, n, max_dist, w->site, w->start);
+    envelope_fill(w->fv, w->featv, n, max_dist, w->site, w->start, cnt,
+                  w->out, w->featout);
     for (long j = 0; j < n; ++j) {
-        d[j * stride] = out[j];
-        feat[j * stride] = featout[j];
+        d[j * stride] = w->out[j];
+        feat[j * stride] = w->featout[j];
     }
 }
 
-/* 2-D EEDT of an M x L image (Sec. 3.1 column scans, then the Sec. 3.3.1
+/* 2-D EEDT of an M x L image (Sec. 3.1 column distances, then the Sec. 3.3.1
  * envelope per row).  D and F are M*L int32 arrays; F may be NULL.
  * Returns 0, or -1 when memory runs out. */
 int oracle_edt2d(const uint8_t *mask, int M, int L, int mode, int32_t *D,
@@ -231,33 +263,25 @@ int oracle_edt2d(const uint8_t *mask, int M, int L, int mode, int32_t *D,
     int64_t max_dist = oracle_max_dist(2, shape);
     int64_t *d = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int32_t *feat = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-    long line = L > M ? L : M;
-    int64_t *fv = malloc(sizeof(int64_t) * (size_t)line);
-    int32_t *featv = malloc(sizeof(int32_t) * (size_t)line);
-    int64_t *out = malloc(sizeof(int64_t) * (size_t)line);
-    int32_t *featout = malloc(sizeof(int32_t) * (size_t)line);
-    int64_t *ks = malloc(sizeof(int64_t) * (size_t)(line + 1));
-    int64_t *js = malloc(sizeof(int64_t) * (size_t)(line + 2));
-    int rc = 0;
-    if (!d || !feat || !fv || !featv || !out || !featout || !ks || !js) {
+    line_work w;
+    int rc = work_alloc(&w, L > M ? L : M);
+    if (!d || !feat || rc != 0) {
         rc = -1;
         goto done;
     }
     init_sources(mask, n, mode, max_dist, d, feat);
     for (long j = 0; j < L; ++j)
-        column_scan(d + j, feat + j, M, L, 0);
+        column_nearest(d + j, feat + j, M, L, 0, w.above);
     for (long i = 0; i < M; ++i)
-        envelope_pass(d + i * L, feat + i * L, L, 1, max_dist, fv, featv,
-                      out, featout, ks, js);
+        envelope_pass(d + i * L, feat + i * L, L, 1, max_dist, &w);
     finish(d, feat, n, max_dist, D, F);
 done:
-    free(d); free(feat); free(fv); free(featv); free(out); free(featout);
-    free(ks); free(js);
+    free(d); free(feat); work_free(&w);
     return rc;
 }
 
-/* 3-D EEDT of a Dz x H x W volume: the column scans of Sec. 3.1 along z, then
- * the envelope of Sec. 3.3.1 along y and along x. */
+/* 3-D EEDT of a Dz x H x W volume: the column distances of Sec. 3.1 along z,
+ * then the envelope of Sec. 3.3.1 along y and along x. */
 int oracle_edt3d(const uint8_t *mask, int Dz, int H, int W, int mode,
                  int32_t *D, int32_t *F)
 {
@@ -270,62 +294,61 @@ int oracle_edt3d(const uint8_t *mask, int Dz, int H, int W, int mode,
     if (W > line) line = W;
     int64_t *d = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int32_t *feat = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-    int64_t *fv = malloc(sizeof(int64_t) * (size_t)line);
-    int32_t *featv = malloc(sizeof(int32_t) * (size_t)line);
-    int64_t *out = malloc(sizeof(int64_t) * (size_t)line);
-    int32_t *featout = malloc(sizeof(int32_t) * (size_t)line);
-    int64_t *ks = malloc(sizeof(int64_t) * (size_t)(line + 1));
-    int64_t *js = malloc(sizeof(int64_t) * (size_t)(line + 2));
-    int rc = 0;
-    if (!d || !feat || !fv || !featv || !out || !featout || !ks || !js) {
+    line_work w;
+    int rc = work_alloc(&w, line);
+    if (!d || !feat || rc != 0) {
         rc = -1;
         goto done;
     }
     init_sources(mask, n, mode, max_dist, d, feat);
     for (long p = 0; p < plane; ++p)
-        column_scan(d + p, feat + p, Dz, plane, 0);
+        column_nearest(d + p, feat + p, Dz, plane, 0, w.above);
     for (long z = 0; z < Dz; ++z)
         for (long x = 0; x < W; ++x)
             envelope_pass(d + z * plane + x, feat + z * plane + x, H, W,
-                          max_dist, fv, featv, out, featout, ks, js);
+                          max_dist, &w);
     for (long z = 0; z < Dz; ++z)
         for (long y = 0; y < H; ++y)
             envelope_pass(d + z * plane + y * W, feat + z * plane + y * W, W,
-                          1, max_dist, fv, featv, out, featout, ks, js);
+                          1, max_dist, &w);
     finish(d, feat, n, max_dist, D, F);
 done:
-    free(d); free(feat); free(fv); free(featv); free(out); free(featout);
-    free(ks); free(js);
+    free(d); free(feat); work_free(&w);
     return rc;
 }
 
-/* The column scans alone on an M x L image (Fig. 19 after the downward scan
- * when down_only != 0, Fig. 18(b) after both scans).  Dv receives the int64 squared
- * vertical distances (max_dist = infinity), G the feature index. */
+/* The column distances alone on an M x L image (Fig. 19 when down_only != 0:
+ * sources at or above only; Fig. 18(b) otherwise).  Dv receives the int64
+ * squared vertical distances (max_dist = infinity), G the feature index. */
 int oracle_column_pass2d(const uint8_t *mask, int M, int L, int mode,
                          int down_only, int64_t *Dv, int32_t *G)
 {
     long n = (long)M * L;
     int shape[2] = {M, L};
     int64_t max_dist = oracle_max_dist(2, shape);
+    long *above = malloc(sizeof(long) * (size_t)(M > 0 ? M : 1));
+    if (!above)
+        return -1;
     init_sources(mask, n, mode, max_dist, Dv, G);
     for (long j = 0; j < L; ++j)
-        column_scan(Dv + j, G + j, M, L, down_only);
+        column_nearest(Dv + j, G + j, M, L, down_only, above);
+    free(above);
     return 0;
 }
 
-/* The first scan of Sec. 3.3.1 on one line f[0..n-1] (values >= max_dist are
- * infinite).  Writes the contributors ks[0..cnt-1] and the starts js[0..cnt]
- * (0-based) and returns cnt. */
+/* The envelope list of Sec. 3.3.1 on one line f[0..n-1] (values >= max_dist
+ * are infinite): the listed positions site[0..cnt-1] with their first
+ * positions start[0..cnt] (0-based, start[cnt] = n).  Returns cnt. */
 long oracle_envelope_state(const int64_t *f, long n, int64_t max_dist,
-                           int64_t *ks, int64_t *js)
+                           int64_t *site, int64_t *start)
 {
-    return envelope_scan(f, n, 1, max_dist, ks, js);
+    return lower_envelope(f, n, max_dist, site, start);
 }
 
-/* The basic O(M L^2) row processing of Sec. 3.1 (row part of Listing 7), after the same column scans: each position starts
- * from its own vertical distance and takes any strictly smaller combination
- * D_v(k) + (k - j)^2.  A second, independent row pass for cross-checks. */
+/* The basic O(M L^2) row processing of Sec. 3.1, after the same column
+ * distances: each position starts from its own vertical distance and takes
+ * any strictly smaller combination D_v(k) + (k - j)^2 (Eq. (5) minimised by
+ * trying every k).  A second, independent row pass for cross-checks. */
 int oracle_edt2d_basic(const uint8_t *mask, int M, int L, int mode,
                        int32_t *D, int32_t *F)
 {
@@ -336,14 +359,15 @@ int oracle_edt2d_basic(const uint8_t *mask, int M, int L, int mode,
     int32_t *feat = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     int64_t *v = malloc(sizeof(int64_t) * (size_t)(L > 0 ? L : 1));
     int32_t *fv = malloc(sizeof(int32_t) * (size_t)(L > 0 ? L : 1));
+    long *above = malloc(sizeof(long) * (size_t)(M > 0 ? M : 1));
     int rc = 0;
-    if (!d || !feat || !v || !fv) {
+    if (!d || !feat || !v || !fv || !above) {
         rc = -1;
         goto done;
     }
     init_sources(mask, n, mode, max_dist, d, feat);
     for (long j = 0; j < L; ++j)
-        column_scan(d + j, feat + j, M, L, 0);
+        column_nearest(d + j, feat + j, M, L, 0, above);
     for (long i = 0; i < M; ++i) {
         for (long k = 0; k < L; ++k) {
             v[k] = d[i * L + k];
@@ -365,12 +389,12 @@ int oracle_edt2d_basic(const uint8_t *mask, int M, int L, int mode,
     }
     finish(d, feat, n, max_dist, D, F);
 done:
-    free(d); free(feat); free(v); free(fv);
+    free(d); free(feat); free(v); free(fv); free(above);
     return rc;
 }
 
-/* Sec. 3.1: "the square root can be drawn after all squared distances have
- * been determined".  Reading: the float32 nearest to sqrt(D).  The square
+/* Sec. 3.1 notes that the square root is only needed once, after all squared
+ * distances are known.  Reading: the float32 nearest to sqrt(D).  The square
  * root is taken in double and rounded once to float; for integers below 2^31
  * this double rounding cannot differ from a single correct rounding (53 >=
  * 2*24 + 2).  D = INT32_MAX (no source) maps to +infinity. */

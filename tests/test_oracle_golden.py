@@ -72,9 +72,15 @@ def test_fig21_candidate_rows_match_oracle_minimum():
 
 
 def test_sec331_envelope_state():
-    """Sec. 3.3.1 walk-through: js = (1,1,7,11), ks = (1,5,8) on row 1."""
+    """Sec. 3.3.1 walk-through on row 1: the paper's state js = (1,1,7,11),
+    ks = (1,5,8) starts with its dummy first parabola at column 1, whose
+    interval [1, 1) is empty; the oracle lists no dummy, so its state must be
+    the rest: columns 5 and 8 from positions 1 and 7, the line ending at 11."""
     g = keyed("sec331_envelope_state.txt")
+    ks_paper = [int(v) for v in g["ks"]]
+    js_paper = [int(v) for v in g["js"]]
+    assert js_paper[0] == js_paper[1]          # the dummy owns no position
     Dv, _, maxd = oracle.column_pass(six_object_mask(), oracle.TO_OBJECT)
-    ks, js = oracle.envelope_state(Dv[0], maxd)
-    np.testing.assert_array_equal(ks + 1, [int(v) for v in g["ks"]])
-    np.testing.assert_array_equal(js + 1, [int(v) for v in g["js"]])
+    site, start = oracle.envelope_state(Dv[0], maxd)
+    np.testing.assert_array_equal(site + 1, ks_paper[1:])
+    np.testing.assert_array_equal(start + 1, js_paper[1:])

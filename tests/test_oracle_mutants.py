@@ -15,21 +15,21 @@ from golden_io import grid, six_object_mask
 SRC = os.path.join(os.path.dirname(oracle.__file__), "edt_oracle.c")
 
 MUTANTS = {
-    "dist_step_plus_one": ("dist_step += 2;", "dist_step += 1;"),
-    "no_step_reset": ("            dist_step = 1;\n        }\n    }\n    if (down_only)",
-                      "            dist_step = dist_step;\n        }\n    }\n    if (down_only)"),
-    "no_upward_scan": ("    if (down_only)\n        return;", "    return;"),
-    "intersection_sign": ("- k * k + l * l", "+ k * k - l * l"),
-    "intersection_denominator": ("2 * (l - k)", "(l - k)"),
+    # column distances (Sec. 3.1)
+    "no_upward_sweep": ("long dn = down_only ? -1 : next;", "long dn = -1;"),
+    "no_downward_sweep": ("if (dn < 0 || (up >= 0 &&", "if (0 && (up >= 0 &&"),
+    "distance_not_squared": ("(int64_t)(i - g) * (int64_t)(i - g);", "(int64_t)(i - g) * (int64_t)(i > g ? 1 : -1);"),
+    "stale_nearest_below": ("        if (d[i * stride] == 0)\n            next = i;",
+                            "        if (d[i * stride] == 0 && next < 0)\n            next = i;"),
+    # envelope (Sec. 3.3.1, Eq. (5) and (6))
+    "intersection_sign": ("f[m] - f[k] + m * m - k * k", "f[m] - f[k] - m * m + k * k"),
+    "intersection_denominator": ("2 * (m - k));", "(m - k));"),
     "floor_not_ceil": ("if (num > 0 && num % den != 0)", "if (num < 0 && num % den != 0)"),
-    "strict_pop": ("while (j <= js[idx])", "while (j < js[idx])"),
-    "no_pop": ("while (j <= js[idx])", "while (0 && j <= js[idx])"),
-    "drop_border_check": ("if (j <= n - 1) {", "if (1) {"),
-    "no_start_clamp": ("js[idx] = j > 0 ? j : 0;", "js[idx] = j;"),
-    "fill_wrong_offset": ("(j - k) * (j - k);\n            if (f[k * stride] >= max_dist",
-                          "(j - k + 1) * (j - k);\n            if (f[k * stride] >= max_dist"),
-    "feature_from_target": ("feat_out[j * stride] = feat_in[k * stride];",
-                            "feat_out[j * stride] = feat_in[j * stride];"),
+    "strict_pop": ("if (s > start[cnt - 1])", "if (s >= start[cnt - 1])"),
+    "no_pop": ("while (cnt > 0) {", "while (0 && cnt > 0) {"),
+    "first_site_not_at_zero": ("            cnt -= 1;\n            s = 0;", "            cnt -= 1;\n            s = m;"),
+    "fill_wrong_offset": ("out[j] = f[k] + (j - k) * (j - k);", "out[j] = f[k] + (j - k + 1) * (j - k);"),
+    "feature_from_target": ("feat_out[j] = feat_in[k];", "feat_out[j] = feat_in[j];"),
     "wrong_axis_3d": ("envelope_pass(d + z * plane + x, feat + z * plane + x, H, W,",
                       "envelope_pass(d + z * plane + x, feat + z * plane + x, H, 1,"),
     "mode_ignored": ("(mode == ORACLE_TO_OBJECT) ? (mask[p] != 0) : (mask[p] == 0)",
@@ -58,7 +58,8 @@ def _build(tmp_path, name, old, new):
 
 
 def _envelope_state_row1(lib):
-    """ks, js (1-based) of the Sec. 3.3.1 walk-through, from the variant."""
+    """Listed columns and their first positions (1-based, with the line end)
+    of the Sec. 3.3.1 walk-through row, from the variant."""
     m = six_object_mask()
     Dv = np.empty(m.shape, np.int64)
     G = np.empty(m.shape, np.int32)
@@ -66,13 +67,13 @@ def _envelope_state_row1(lib):
                              Dv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                              G.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     f = np.ascontiguousarray(Dv[0])
-    ks = np.zeros(12, np.int64)
-    js = np.zeros(13, np.int64)
+    site = np.zeros(12, np.int64)
+    start = np.zeros(12, np.int64)
     cnt = lib.oracle_envelope_state(f.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 10,
                                     oracle.max_dist((9, 10)),
-                                    ks.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                    js.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
-    return (ks[:cnt] + 1).tolist(), (js[:cnt + 1] + 1).tolist()
+                                    site.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    start.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return (site[:cnt] + 1).tolist(), (start[:cnt + 1] + 1).tolist()
 
 
 def _run(lib, m, mode):
@@ -93,12 +94,12 @@ def _pins_pass(lib):
     D, F = _run(lib, six_object_mask(), 0)
     if not np.array_equal(D, grid("fig18c_final.txt")):
         return False
-    # Fig. 21 ties '2/5' and '5/8' resolved to the right-hand parabola (the
-    # "j <= js" pop of the fast algorithm)
+    # Fig. 21 ties '2/5' and '5/8' resolved to the right-hand parabola
     if not np.array_equal(F[0] % 10 + 1, [5, 5, 5, 5, 5, 5, 8, 8, 8, 8]):
         return False
-    # Sec. 3.3.1 walk-through: ks = (1, 5, 8), js = (1, 1, 7, 11)
-    if _envelope_state_row1(lib) != ([1, 5, 8], [1, 1, 7, 11]):
+    # Sec. 3.3.1 walk-through: ks = (1, 5, 8), js = (1, 1, 7, 11) without the
+    # paper's dummy first parabola (its interval [1, 1) is empty)
+    if _envelope_state_row1(lib) != ([5, 8], [1, 7, 11]):
         return False
     rng = np.random.default_rng(0)
     for t in range(60):

@@ -74,7 +74,7 @@ edt_status edt_sq2d(const uint8_t *mask, int H, int W, int mode, int32_t *D,
                     edt_stream_t stream);
 
 /* Squared 3-D EDT of a [Dz][H][W] volume (the same method applied along z,
- * y and x; Sec. 3.1 "separate processing of all dimensions"). */
+ * y and x; Sec. 3.1 treats the axes one after another). */
 edt_status edt_sq3d(const uint8_t *mask, int Dz, int H, int W, int mode,
                     int32_t *D, edt_stream_t stream);
 

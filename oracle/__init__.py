@@ -81,7 +81,7 @@ def _load():
             fn.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p]
         lib.oracle_danielsson2d.restype = ctypes.c_int
         lib.oracle_danielsson2d.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                            i32p, i32p, i32p]
+                                            ctypes.c_int, i32p, i32p, i32p]
         _lib = lib
         return lib
 
@@ -196,10 +196,13 @@ def cityblock_4scan(mask, mode: int = TO_OBJECT, stop_after_columns: bool = Fals
     return _nedt("oracle_cityblock2d_4scan", mask, mode, stop_after_columns)
 
 
-def danielsson(mask, mode: int = TO_OBJECT, stop_after_forward: bool = False):
+def danielsson(mask, mode: int = TO_OBJECT, stop_after_forward: bool = False, text_order: bool = False):
     """Danielsson's approximate Euclidean transform, Sec. 2.3 (two scans of
     relative-position propagation): (D, DY, DX), D = DY^2 + DX^2 in int32,
-    INT32_MAX and DY = DX = -1 where no position arrived."""
+    INT32_MAX and DY = DX = -1 where no position arrived.  text_order: in the
+    right-to-left pass of the first scan, look at the right neighbour before
+    the upper-right one (the order the paper's text names; its listing, the
+    default, has them the other way round)."""
     lib = _load()
     m = _mask(mask)
     assert m.ndim == 2
@@ -207,7 +210,8 @@ def danielsson(mask, mode: int = TO_OBJECT, stop_after_forward: bool = False):
     DY = np.empty(m.shape, dtype=np.int32)
     DX = np.empty(m.shape, dtype=np.int32)
     if lib.oracle_danielsson2d(_ptr(m, ctypes.c_uint8), m.shape[0], m.shape[1], int(mode),
-                               int(stop_after_forward), _ptr(D, ctypes.c_int32), _ptr(DY, ctypes.c_int32),
+                               int(stop_after_forward), int(bool(text_order)), _ptr(D, ctypes.c_int32),
+                               _ptr(DY, ctypes.c_int32),
                                _ptr(DX, ctypes.c_int32)) != 0:
         raise MemoryError("oracle ran out of memory")
     return D, DY, DX

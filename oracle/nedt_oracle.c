@@ -155,16 +155,19 @@ int oracle_chamfer43_2d(const uint8_t *mask, int M, int L, int mode, int stop, i
  *   (a) every column: the lower neighbour;
  *   (b) left to right: the left, then the lower-left one;
  *   (c) right to left: the right, then the lower-right one.
- * Readings: inside (c) of the forward scan the upper-right neighbour comes
- * first, as in the paper's listing (its text names the right neighbour
- * first); a single-row image is visited by neither scan, so only its
- * sources get a position.
+ * Readings: inside (c) of the forward scan the paper's listing looks at the
+ * upper-right neighbour first and its text names the right neighbour first;
+ * `order` selects the listing's order (0, the default reading) or the text's
+ * (1).  Only ties of length between the two looks depend on it, and no mask
+ * of up to 24 pixels tells them apart; the accuracy against the exact
+ * transform is reported under both.  A single-row image is visited by
+ * neither scan, so only its sources get a position.
  * Pins: Fig. 16(b) and 16(c) fix the passes, the increments and the strict
- * comparison (a plant of any of those fails them), and the tests check the
- * invariants below.  The order of the two looks inside (b) and (c) and the
- * diagonal looks themselves do not change the example's result (they matter
- * only at ties and in rare configurations): for those details parity is
- * unpinned.
+ * comparison (a plant of any of those fails them); a 4 x 4 mask derived by
+ * hand from the text fixes the diagonal looks (without them one cell ends at
+ * 9 instead of 8); the tests check the invariants below.  The order of the
+ * two looks inside (b) and (c) is unpinned: no example within reach of a
+ * hand derivation separates the orders.
  * stop = 1 returns the state after the forward scan (Fig. 16(b)).
  * Out: D = dy^2 + dx^2 (INT32_MAX without a position), DY, DX (-1 there).
  */
@@ -189,8 +192,9 @@ static void take(RelPos *r, long p, long q, int sy, int sx)
     }
 }
 
-/* one row of a scan; v = -1 looks at the row above, +1 at the row below */
-static void danielsson_row(RelPos *r, int i, int v)
+/* one row of a scan; v = -1 looks at the row above, +1 at the row below;
+ * order 1 looks right before upper-right in (c) of the forward scan */
+static void danielsson_row(RelPos *r, int i, int v, int order)
 {
     const int L = r->L;
     const long row = (long)i * L, nb = (long)(i + v) * L;
@@ -200,7 +204,7 @@ static void danielsson_row(RelPos *r, int i, int v)
         take(r, row + j, nb + j - 1, 1, 1);
     }
     for (int j = L - 2; j >= 0; --j) {
-        if (v < 0) {
+        if (v < 0 && order == 0) {
             take(r, row + j, nb + j + 1, 1, 1);
             take(r, row + j, row + j + 1, 0, 1);
         } else {
@@ -210,8 +214,8 @@ static void danielsson_row(RelPos *r, int i, int v)
     }
 }
 
-int oracle_danielsson2d(const uint8_t *mask, int M, int L, int mode, int stop, int32_t *D, int32_t *DY,
-                        int32_t *DX)
+int oracle_danielsson2d(const uint8_t *mask, int M, int L, int mode, int stop, int order, int32_t *D,
+                        int32_t *DY, int32_t *DX)
 {
     const long n = (long)M * L;
     RelPos r;
@@ -224,9 +228,9 @@ int oracle_danielsson2d(const uint8_t *mask, int M, int L, int mode, int stop, i
         return 1;
     }
     for (long p = 0; p < n; ++p) r.dy[p] = r.dx[p] = is_source(mask, p, mode) ? 0 : -1;
-    for (int i = 1; i < M; ++i) danielsson_row(&r, i, -1);
+    for (int i = 1; i < M; ++i) danielsson_row(&r, i, -1, order);
     if (!stop)
-        for (int i = M - 2; i >= 0; --i) danielsson_row(&r, i, +1);
+        for (int i = M - 2; i >= 0; --i) danielsson_row(&r, i, +1, order);
     for (long p = 0; p < n; ++p) {
         const int64_t len = rel_len(&r, p);
         D[p] = len == INT64_MAX || len > INT32_MAX ? INT32_MAX : (int32_t)len;

@@ -1,5 +1,5 @@
-// 3-D exact EDT.  The paper processes the dimensions one after the other
-// (Sec. 3.1: methods "based on the separate processing of all dimensions");
+// 3-D exact EDT.  Sec. 3.1 of the paper handles a multi-dimensional image one
+// axis at a time;
 // for a [Dz][H][W] volume this library runs
 //   (z) the column pass along z: the volume seen as a 2-D image with Dz rows
 //       and H*W columns, handled by the same column-bit kernel as 2-D images;

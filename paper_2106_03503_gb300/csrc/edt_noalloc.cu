@@ -13,6 +13,7 @@
 // GPU that loads the library, until the process exits, and it is shared by all
 // calls: calls that overlap on the GPU (different streams, or different host
 // threads without ordering) race on it and must be serialised by the caller.
+#include <atomic>
 #include <mutex>
 
 #include "edt_internal.h"
@@ -37,7 +38,8 @@ edt_status run_transform(const uint8_t* mask, int ndim, const int* shape, int mo
 
 // Device address of the scratch array, resolved once per device with that
 // device current (the host-side symbol is only a stand-in, not an address).
-static void* g_noalloc_ptr[64];
+// After the first call on a device the address is read without the lock.
+static std::atomic<void*> g_noalloc_ptr[64];
 static std::mutex g_noalloc_mu;
 
 static edt_status noalloc_scratch(void** out)
@@ -46,14 +48,17 @@ static edt_status noalloc_scratch(void** out)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(EDT_ERR_CUDA, "device index %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (static scratch)");
-        g_noalloc_ptr[dev] = p;
+    void* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (static scratch)");
+            g_noalloc_ptr[dev].store(p, std::memory_order_release);
+        }
     }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return EDT_OK;
 }
 

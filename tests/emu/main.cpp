@@ -6,8 +6,11 @@
 //   emu 2d PART NPARTS   2-D cases whose index is PART modulo NPARTS
 //   emu 3d               3-D cases
 //   emu batch            batches through the persistent kernels
+//   emu maurer           the engine's hull test hidden() against Maurer's
+//                        separating-line removal test on exhaustive triples
 #include "shim.h"
 #include "src/edt_internal.h"
+#include "src/edt_engine.cuh"
 extern "C" {
 int oracle_edt2d(const uint8_t* mask, int M, int L, int mode, int32_t* D, int32_t* F);
 int oracle_edt3d(const uint8_t* mask, int Z, int M, int L, int mode, int32_t* D, int32_t* F);
@@ -226,8 +229,67 @@ static int run_chamfer(int H, int W, double p, int mode)
     return bad;
 }
 
+// Maurer, Qi and Raghavan (2003), "A linear time algorithm for computing exact
+// Euclidean distance transforms of binary images in arbitrary dimensions",
+// the removal test of their row pass: with sites at u < v < w on the line,
+// squared distances f(u), f(v), f(w) from the line to them, a = v - u,
+// b = w - v and c = a + b, site v is removed (its parabola never gives the
+// minimum) when  c f(v) - b f(u) - a f(w) - a b c > 0.  The paper's Sec. 4
+// names this approach as an alternative to the one of Sec. 3.3.1.
+static long long maurer_lhs(long long u, long long fu, long long v, long long fv, long long w, long long fw)
+{
+    const long long a = v - u, b = w - v, c = a + b;
+    return c * fv - b * fu - a * fw - a * b * c;
+}
+
+// For every triple u < v < w < n and every f in 0..fmax (plus a spread of
+// larger values), the engine's hidden() must equal Maurer's removal test
+// except where the three parabolas meet in one point (left-hand side 0),
+// where hidden() removes v and Maurer keeps it; there the envelope's value
+// at every integer position is the same with and without v.
+static int run_maurer(int n, int fmax)
+{
+    std::vector<long long> fs;
+    for (int f = 0; f <= fmax; ++f) fs.push_back(f);
+    for (long long f : {20LL, 25LL, 49LL, 100LL, 101LL, 250LL, 1000LL, 4095LL, 65536LL, 1LL << 24}) fs.push_back(f);
+    long long agree = 0, coincide = 0, bad = 0;
+    for (int u = 0; u < n; ++u)
+        for (int v = u + 1; v < n; ++v)
+            for (int w = v + 1; w < n; ++w)
+                for (long long fu : fs)
+                    for (long long fv : fs)
+                        for (long long fw : fs) {
+                            const bool h = edt::hidden(u, (int)(fu + u * u), v, (int)(fv + v * v), w,
+                                                       (int)(fw + w * w));
+                            const long long lhs = maurer_lhs(u, fu, v, fv, w, fw);
+                            const bool remove = lhs > 0;
+                            if (h == remove) { ++agree; continue; }
+                            if (lhs == 0 && h) {
+                                ++coincide;
+                                // v never lies strictly below both u and w
+                                for (int j = -2 * n; j <= 3 * n; ++j) {
+                                    const long long pu = fu + (long long)(j - u) * (j - u);
+                                    const long long pv = fv + (long long)(j - v) * (j - v);
+                                    const long long pw = fw + (long long)(j - w) * (j - w);
+                                    if (pv < std::min(pu, pw)) { ++bad; break; }
+                                }
+                                continue;
+                            }
+                            if (bad < 5)
+                                fprintf(stderr, "hidden %d vs Maurer %d at u %d v %d w %d f %lld %lld %lld\n", h,
+                                        remove, u, v, w, fu, fv, fw);
+                            ++bad;
+                        }
+    printf("maurer triples agree %lld coincide %lld bad %lld\n", agree, coincide, bad);
+    return bad != 0;
+}
+
 int main(int argc, char** argv)
 {
+    if (argc > 1 && !strcmp(argv[1], "maurer")) {
+        const int n = argc > 2 ? atoi(argv[2]) : 64, fmax = argc > 3 ? atoi(argv[3]) : 12;
+        return run_maurer(n, fmax);
+    }
     if (argc > 1 && !strcmp(argv[1], "chamfer")) {
         const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
         int bad = 0, cases = 0, run = 0;

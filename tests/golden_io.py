@@ -42,6 +42,26 @@ def pairs(name):
     return np.array(dy, dtype=np.int64), np.array(dx, dtype=np.int64)
 
 
+def sections(name):
+    """A fixture of named sections: a line holding one word starts a section,
+    the lines after it are its grid rows.  Returns {name: [row strings]}."""
+    out, cur = {}, None
+    for line in _lines(name):
+        if len(line.split()) == 1 and not line[0].isdigit() and line not in ("-",):
+            cur = line
+            out[cur] = []
+        else:
+            out[cur].append(line)
+    return out
+
+
+def pair_rows(rows):
+    """'dy,dx' cells of the given rows ('-' = none) as two int arrays."""
+    dy = [[-1 if c == "-" else int(c.split(",")[0]) for c in r.split()] for r in rows]
+    dx = [[-1 if c == "-" else int(c.split(",")[1]) for c in r.split()] for r in rows]
+    return np.array(dy, dtype=np.int64), np.array(dx, dtype=np.int64)
+
+
 def six_object_mask():
     """Fig. 18(a) as a uint8 mask (1 = object)."""
     g = grid("fig18a_init.txt")

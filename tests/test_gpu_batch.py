@@ -1,7 +1,9 @@
-"""Batched transforms (edt_plan_create / edt_batch): every job's D, F and dist
-must be bit-identical to a plain edt_feature call on the same mask, in mixed
-batches of uneven sizes and modes, across plan reuse, and at the full batch
-workload (4096 masks, sides 64..1024, densities 0.001..0.1)."""
+"""Batched transforms (edt_plan_create / edt_batch): every job's D must equal
+the oracle's bit for bit, F must name a nearest source and dist must be the
+correctly rounded square root; and every job is bit-identical to a plain
+edt_feature call on the same mask.  Mixed batches of uneven sizes and modes,
+plan reuse, and the full batch workload (4096 masks, sides 64..1024, densities
+0.001..0.1)."""
 import numpy as np
 import pytest
 
@@ -31,7 +33,18 @@ def _jobs(torch, edt, specs, seed):
 
 def _check(jobs, refs, torch):
     torch.cuda.synchronize()
-    for (m, mode, D, F, dist), (Dr, Fr, dr) in zip(jobs, refs):
+    for k, ((m, mode, D, F, dist), (Dr, Fr, dr)) in enumerate(zip(jobs, refs)):
+        # against the oracle
+        m_np = m.cpu().numpy()
+        Do, _ = oracle.edt(m_np, mode)
+        F_np = F.cpu().numpy()
+        if D is not None:
+            assert np.array_equal(D.cpu().numpy(), Do), k
+        msg = feature_valid_fast(m_np, mode, Do, F_np)
+        assert msg is None, (k, msg)
+        if dist is not None:
+            assert np.array_equal(dist.cpu().numpy().view(np.uint32), oracle.sqrt_f32(Do).view(np.uint32)), k
+        # and bit-identical to the plain call
         if D is not None:
             assert torch.equal(D, Dr)
         assert torch.equal(F, Fr)

@@ -1,11 +1,15 @@
-"""Serving (edt_serve_*): each result is the same served alone and served in
-a mix of concurrent 2-D / 3-D requests of mixed sizes, and equal to a plain
-edt_feature call; budget refusal and bad requests fail at submission."""
+"""Serving (edt_serve_*): each result equals the oracle's (D bit-exact, F a
+nearest source, dist the correctly rounded square root), and is the same
+served alone, served in a mix of concurrent 2-D / 3-D requests of mixed sizes
+and computed by a plain edt_feature call; budget refusal and bad requests fail
+at submission."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle
+from gpu_check import feature_valid_fast
 from paper_2106_03503_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -74,6 +78,17 @@ def test_alone_equals_in_the_mix_equals_plain():
         time.sleep(0.0005)
     srv.close()
     for k in range(len(masks)):
+        # the oracle decides: every served D bit-exact, F a nearest source,
+        # dist the correctly rounded square root
+        m_np = masks[k].numpy()
+        Do, _ = oracle.edt(m_np, k % 2)
+        for D, F, d in (alone[k], mix[k]):
+            D, F, d = D.numpy(), F.numpy(), d.numpy()
+            assert np.array_equal(D, Do), k
+            msg = feature_valid_fast(m_np, k % 2, D, F)
+            assert msg is None, (k, msg)
+            assert np.array_equal(d.view(np.uint32), oracle.sqrt_f32(Do).view(np.uint32)), k
+        # and the same bits alone, in the mix and from a plain call
         for a, b, c in zip(plain[k], alone[k], mix[k]):
             assert torch.equal(a.view(torch.int32), b.view(torch.int32)), k
             assert torch.equal(a.view(torch.int32), c.view(torch.int32)), k

@@ -75,6 +75,20 @@ def test_batch_kernels_match_oracle(emu):
     _run_all([[emu, "batch"]])
 
 
+def test_hull_test_is_maurers_removal_test(emu):
+    """Sec. 4 names the separating-line row pass of Maurer et al. as an
+    alternative; its removal test and the engine's hidden() agree on every
+    triple of sites u < v < w < 64 with vertical distances 0..12 and a spread
+    of larger ones, except where the three parabolas meet in one point, where
+    hidden() drops v and Maurer keeps it -- and there v's parabola is nowhere
+    below the other two, so the distances cannot change."""
+    r = subprocess.run([emu, "maurer", "64", "12"], capture_output=True, text=True, timeout=900,
+                       env=dict(os.environ, ASAN_OPTIONS="detect_leaks=0"))
+    assert r.returncode == 0 and " bad 0" in r.stdout, r.stdout + r.stderr[-3000:]
+    agree, coincide = (int(x) for x in r.stdout.split()[3:6:2])
+    assert agree > 0 and coincide > 0
+
+
 def test_cityblock_kernel_matches_oracle(emu):
     n = max(1, min(8, os.cpu_count() or 1))
     _run_all([[emu, "cityblock", str(k), str(n)] for k in range(n)])

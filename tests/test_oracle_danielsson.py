@@ -3,8 +3,9 @@ propagation), an approximation of the exact EDT kept as an accuracy foil.
 
 Pinned to the paper's worked example (Fig. 16(b) after the first scan,
 Fig. 16(c) final, one printed cell read as a typo; the paper states that the
-example's result equals the exact transform of Fig. 18(c)), to what the
-propagation guarantees (every value is the squared length of an offset that
+example's result equals the exact transform of Fig. 18(c)), to a 4 x 4 mask
+whose result was derived by hand from the text and depends on the diagonal
+looks, to what the propagation guarantees (every value is the squared length of an offset that
 dominates the offset to some source componentwise, so it is never below the
 exact squared distance; a single source is reached exactly), and measured
 against the exact oracle on the synthetic workloads: how often and by how much
@@ -13,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
-from golden_io import grid, pairs, six_object_mask
+from golden_io import grid, pair_rows, pairs, sections, six_object_mask
 from paper_2106_03503_gb300 import inputs
 
 INF = np.iinfo(np.int32).max
@@ -40,6 +41,27 @@ def test_fig16c_final():
     np.testing.assert_array_equal(DY, ey)
     np.testing.assert_array_equal(DX, ex)
     np.testing.assert_array_equal(D, DY * DY + DX * DX)
+
+
+def test_hand_derived_diagonal_example():
+    """The text's diagonal looks (upper-left in the left-to-right pass,
+    upper-right in the right-to-left pass; mirrored in the second scan) decide
+    one cell of this 4 x 4 mask: (2,2), D = 8, instead of (0,3), D = 9.  Both
+    look orders give the same grids here."""
+    g = sections("danielsson_diagonal_4x4.txt")
+    m = np.array([[int(c) for c in r.split()] for r in g["mask"]], np.uint8)
+    for text_order in (False, True):
+        _, fy, fx = oracle.danielsson(m, 0, stop_after_forward=True, text_order=text_order)
+        ey, ex = pair_rows(g["forward"])
+        np.testing.assert_array_equal(fy, ey)
+        np.testing.assert_array_equal(fx, ex)
+        D, DY, DX = oracle.danielsson(m, 0, text_order=text_order)
+        ey, ex = pair_rows(g["final"])
+        np.testing.assert_array_equal(DY, ey)
+        np.testing.assert_array_equal(DX, ex)
+        assert D[3, 3] == 8
+    De, _ = oracle.edt(m, 0)
+    np.testing.assert_array_equal(D, De)       # exact on this example
 
 
 def test_example_equals_the_exact_transform():
@@ -86,8 +108,8 @@ def test_single_row_is_not_visited():
     np.testing.assert_array_equal(D, [[INF, 0, INF, INF, 0]])
 
 
-def _accuracy(m, mode):
-    D, _, _ = oracle.danielsson(m, mode)
+def _accuracy(m, mode, text_order):
+    D, _, _ = oracle.danielsson(m, mode, text_order=text_order)
     De, _ = oracle.edt(m, mode)
     diff = D != De
     err = np.sqrt(D[diff].astype(np.float64)) - np.sqrt(De[diff].astype(np.float64))
@@ -97,14 +119,18 @@ def _accuracy(m, mode):
 def test_accuracy_on_the_workloads(capsys):
     """How often and by how much the approximation differs from the exact
     transform: the 512^2 Bernoulli points and both transforms of the 8192^2
-    discs mask (the 2-D workloads; the paper gives the method for 2-D only)."""
+    discs mask (the 2-D workloads; the paper gives the method for 2-D only),
+    under both readings of the look order (the listing's and the text's),
+    which the paper's example does not tell apart."""
     rows = []
-    n, e = _accuracy(inputs.points_512(), 0)
-    rows.append(("512^2 points p=0.01, to object", n, 512 * 512, e))
     discs = inputs.discs_8192()
-    for mode, name in ((0, "to object"), (1, "to background")):
-        n, e = _accuracy(discs, mode)
-        rows.append((f"8192^2 discs, {name}", n, discs.size, e))
+    for text_order in (False, True):
+        reading = "text order" if text_order else "listing order"
+        n, e = _accuracy(inputs.points_512(), 0, text_order)
+        rows.append((f"512^2 points p=0.01, to object, {reading}", n, 512 * 512, e))
+        for mode, name in ((0, "to object"), (1, "to background")):
+            n, e = _accuracy(discs, mode, text_order)
+            rows.append((f"8192^2 discs, {name}, {reading}", n, discs.size, e))
     with capsys.disabled():
         for name, n, px, e in rows:
             print(f"\nDanielsson vs exact, {name}: {n} of {px} pixels differ "

@@ -1,4 +1,4 @@
-"""The float32 square root of Sec. 3.1 ("drawn after all squared distances"),
+"""The float32 square root of Sec. 3.1 (taken once the squared distances are known),
 checked for correct rounding with exact midpoint arithmetic."""
 import numpy as np
 

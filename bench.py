@@ -119,19 +119,66 @@ def issue_roofline(kernel: str, launch_s: float, sm_mhz: float, sms: int):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled during the timed
+    region: through NVML (read-only queries, every 2 ms, so that even a timed
+    region of a few milliseconds gets samples), else nvidia-smi every 100 ms."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReason bits (nvml.h)
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40}
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
         self.t = None
+        self.nvml = None
+        self.samples = []        # (sm_mhz, max_mhz, reason bits)
+        self.running = False
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            # the PCI order of CUDA_VISIBLE_DEVICES is the process's device 0..;
+            # NVML counts all devices, so map through the UUID when one is set
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            first = vis.split(",")[self.gpu].strip() if vis else ""
+            if first.startswith("GPU-"):
+                if lib.nvmlDeviceGetHandleByUUID(first.encode(), ctypes.byref(h)) != 0:
+                    return None
+            else:
+                idx = int(first) if first.isdigit() else self.gpu
+                if lib.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(h)) != 0:
+                    return None
+            return lib, h
+        except Exception:
+            return None
+
+    def _nvml_loop(self):
+        import ctypes
+        lib, h = self.nvml
+        mhz, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while self.running:
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    lib.nvmlDeviceGetCurrentClocksEventReasons(h, ctypes.byref(rs)) == 0):
+                self.samples.append((mhz.value, mx.value, rs.value))
+            time.sleep(0.002)
 
     def start(self):
+        self.nvml = self._nvml_open()
+        if self.nvml is not None:
+            self.running = True
+            self.t = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.t.start()
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
@@ -152,6 +199,14 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            self.running = False
+            self.t.join(timeout=1)
+            smp = list(self.samples)
+            reasons = sorted(nm for nm, bit in self.REASON_BITS.items() if any(r & bit for _, _, r in smp))
+            return {"sm_mhz": statistics.median([m for m, _, _ in smp]) if smp else None,
+                    "sm_max_mhz": max(x for _, x, _ in smp) if smp else None,
+                    "reasons": reasons, "samples": len(smp), "source": "nvml, every 2 ms"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
                     "samples": 0}
@@ -207,6 +262,22 @@ def cpu_oracle_rate(mask, repeats=1):
         oracle.edt(mask, 1)
     dt = time.perf_counter() - t0
     return 2 * mask.size * repeats / dt / 1e9, dt
+
+
+def cpu_oracle_rate_all_cores(mask, repeats=1):
+    """The same with the OpenMP build of the oracle's source (independent
+    columns and rows over all host cores): (Gpixel/s, seconds, threads), or
+    None without OpenMP."""
+    import oracle
+    if oracle.edt_all_cores(mask[:64], 0) is None:
+        return None
+    t0 = time.perf_counter()
+    threads = 0
+    for _ in range(repeats):
+        threads = oracle.edt_all_cores(mask, 0)[2]
+        oracle.edt_all_cores(mask, 1)
+    dt = time.perf_counter() - t0
+    return 2 * mask.size * repeats / dt / 1e9, dt, threads
 
 
 def oracle_beside(fn, pixels, sample):
@@ -392,102 +463,129 @@ def measure_nedt(edt, torch, dev, mask_np, kind, reps=20):
             "effective_gbs_5B_per_px": 5 * px / (ms / 1e3) / 1e9, "kernel_ms_per_transform": k_ms}
 
 
-def measure_serve(edt, torch, n_jobs=600, warm=200, loads=(0.5, 0.8), seed=5):
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(round(q * (len(v) - 1))))] if v else None
+
+
+def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), pool_size=512, seed=5):
     """Serving: Poisson arrivals of mixed jobs (80 % 2-D squares of side
     128..4096 with Bernoulli density log-uniform 0.001..0.1, 20 % 3-D cubes of
-    side 64..256 of smoothed noise), D+F, host buffers, 40 GB budget.  Masks
-    are drawn from a pool of pre-generated masks of that recipe.  Capacity is
-    measured in pixels per second with a burst of `warm` jobs (after 30
-    untimed ones); each Poisson run's arrival rate is one of `loads` x that
-    capacity divided by the mean size of the jobs that follow, so that the
-    offered load does not depend on which jobs happened to be in the burst.
-    The top-level numbers are those of the last load."""
+    side 64..256 of smoothed noise), D+F, host buffers, 40 GB budget.
+
+    Each job takes one of `pool_size` distinct masks drawn from that recipe
+    beforehand (untimed, pinned).  A burst of `warm` jobs (after 30 untimed
+    ones) measures the capacity in pixels per second; then, for each of
+    `loads`, `n_jobs` jobs arrive as a Poisson stream at load x capacity.  A
+    job's latency runs from its scheduled arrival to the server's completion
+    (so a client that could not submit on time is charged for it); the
+    server's per-ticket record splits it into the wait for admission to a
+    stream and the time on the stream.  The same job stream then runs through
+    the plain path, one synchronous edt_feature_host call per job, back to
+    back: `served_over_plain` = served throughput at load 1.0 / plain."""
     import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
     from paper_2106_03503_gb300 import inputs
     rng = np.random.default_rng(seed)
-    specs = inputs.serving_jobs(48, seed)
-    pool = [torch.from_numpy(inputs.draw_job(j)).pin_memory() for j in specs]
+    specs = inputs.serving_jobs(pool_size, seed)
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        pool = [torch.from_numpy(m).pin_memory() for m in ex.map(inputs.draw_job, specs)]
     maxn = max(m.numel() for m in pool)
-    depth = 24
+    depth = 32
     ring = [(torch.empty(maxn, dtype=torch.int32).pin_memory(),
              torch.empty(maxn, dtype=torch.int32).pin_memory()) for _ in range(depth)]
     srv = edt.Server(40 << 30, n_streams=3)
     free = list(range(depth))
     busy = {}
 
-    def submit(k):
+    def submit(k, t_arrival):
         m = pool[k]
         slot = free.pop()
         D = ring[slot][0][:m.numel()].view(m.shape)
         F = ring[slot][1][:m.numel()].view(m.shape)
+        t_sub = time.perf_counter()
         t = srv.submit(m, 0, out=(D, F, None))
-        busy[t] = (slot, m.numel())
+        busy[t] = (slot, m.numel(), t_arrival, t_sub)
         return t
 
-    def reap(lats):
+    def reap(recs):
         """Collect finished jobs; sleep briefly when none has finished, so
         that polling does not keep the server's lock and a core busy."""
         got = False
         for t in list(busy):
-            r = srv.poll(t)
+            r = srv.poll_detail(t)
             if r is not None:
-                slot, n = busy.pop(t)
+                slot, n, t_arr, t_sub = busy.pop(t)
                 free.append(slot)
-                lats.append((r[0], n))
+                recs.append({"px": n, "late": t_sub - t_arr, "latency": r[0], "wait": r[1]})
                 got = True
         if not got:
             time.sleep(20e-6)
 
-    order = rng.integers(0, len(pool), size=n_jobs + warm)
-
     def burst(ids):
-        lats_b = []
+        recs = []
         k = 0
         t0 = time.perf_counter()
         while k < len(ids) or busy:
             if k < len(ids) and free:
-                submit(int(ids[k]))
+                submit(int(ids[k]), time.perf_counter())
                 k += 1
             else:
-                reap(lats_b)
-        return time.perf_counter() - t0, sum(n for _, n in lats_b)
+                reap(recs)
+        return time.perf_counter() - t0, sum(r["px"] for r in recs)
 
-    burst(rng.integers(0, len(pool), size=30))            # untimed: pools, plans, graphs
-    # capacity: keep `depth` jobs in flight
-    secs, px_burst = burst(order[:warm])
+    burst(rng.integers(0, pool_size, size=30))            # untimed: pools, plans, graphs
+    order = rng.integers(0, pool_size, size=warm + n_jobs)
+    secs, px_burst = burst(order[:warm])                   # warm-up and capacity
     cap_px = px_burst / secs
-    cap = warm / secs
-    # Poisson runs at load x capacity (in pixels), for each load
-    mean_px = float(np.mean([pool[int(k)].numel() for k in order[warm:]]))
+    stream = order[warm:]
+    mean_px = float(np.mean([pool[int(k)].numel() for k in stream]))
     runs = []
     for ld in loads:
         rate = ld * cap_px / mean_px
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
-        lats = []
+        recs = []
         start = time.perf_counter()
         j = 0
         while j < n_jobs or busy:
             now = time.perf_counter() - start
             if j < n_jobs and arrivals[j] <= now and free:
-                submit(int(order[warm + j]))
+                submit(int(stream[j]), start + arrivals[j])
                 j += 1
                 continue
-            reap(lats)
+            reap(recs)
         wall = time.perf_counter() - start
-        ms = sorted(1e3 * l for l, _ in lats)
-        px = sum(n for _, n in lats)
-        runs.append({"load": ld, "arrival_rate_jobs_s": rate, "jobs": len(lats),
-                     "throughput_gpx_s": px / wall / 1e9, "p50_ms": ms[len(ms) // 2],
-                     "p99_ms": ms[min(len(ms) - 1, int(round(0.99 * (len(ms) - 1))))]})
+        lat = [1e3 * (r["late"] + r["latency"]) for r in recs]
+        wait = [1e3 * r["wait"] for r in recs]
+        run_ms = [1e3 * (r["latency"] - r["wait"]) for r in recs]
+        late = [1e3 * r["late"] for r in recs]
+        runs.append({"load": ld, "arrival_rate_jobs_s": rate, "jobs": len(recs),
+                     "throughput_gpx_s": sum(r["px"] for r in recs) / wall / 1e9,
+                     "p50_ms": _pct(lat, 0.5), "p99_ms": _pct(lat, 0.99), "max_ms": max(lat),
+                     "parts_ms": {"client_late_p50": _pct(late, 0.5), "client_late_p99": _pct(late, 0.99),
+                                  "queue_wait_p50": _pct(wait, 0.5), "queue_wait_p99": _pct(wait, 0.99),
+                                  "on_stream_p50": _pct(run_ms, 0.5), "on_stream_p99": _pct(run_ms, 0.99)}})
     srv.close()
+    # the plain path on the same job stream: one synchronous host-buffer call per job
+    t0 = time.perf_counter()
+    for k in stream:
+        m = pool[int(k)]
+        D = ring[0][0][:m.numel()].view(m.shape)
+        F = ring[0][1][:m.numel()].view(m.shape)
+        edt.feature_host(m, 0, D=D, F=F)
+    plain_s = time.perf_counter() - t0
+    plain_gpx = sum(pool[int(k)].numel() for k in stream) / plain_s / 1e9
     main = runs[-1]
     return {"workload": "Poisson stream, 80% 2D side 128-4096 Bernoulli p log-uniform 0.001-0.1, "
                         "20% 3D side 64-256 smoothed noise; 40 GB budget, 3 streams, host buffers",
-            "capacity_jobs_s": cap, "capacity_gpx_s": cap_px / 1e9,
+            "capacity_gpx_s": cap_px / 1e9, "warmup_jobs": warm,
             "load": main["load"], "jobs": main["jobs"], "arrival_rate_jobs_s": main["arrival_rate_jobs_s"],
             "throughput_gpx_s": main["throughput_gpx_s"], "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "plain_gpx_s": plain_gpx, "served_over_plain": main["throughput_gpx_s"] / plain_gpx,
+            "plain": "the same job stream, one synchronous edt_feature_host call per job",
             "sweep": runs,
-            "note": f"{len(pool)} pre-generated masks reused; at most {depth} jobs in flight"}
+            "note": f"{pool_size} distinct masks of the recipe (pinned, drawn untimed), each job one of them; "
+                    f"at most {depth} jobs in flight; latency from the scheduled arrival"}
 
 
 def run_reference(args, rank, world):
@@ -699,6 +797,7 @@ def run_gpu(args, rank, world, local_rank):
         achieved_stores = K2_STORE_BYTES_PER_PX * px_per_k2 / k2_avg_s / 1e9
         traffic = profile_traffic("k_rows2d")
         cpu_val, cpu_s = cpu_oracle_rate(mask_np, repeats=4)     # about 10-15 s of CPU work
+        allc = cpu_oracle_rate_all_cores(mask_np, repeats=4)
         sorted_ms = sorted(step_ms)
         p50 = sorted_ms[len(sorted_ms) // 2]
         p99 = sorted_ms[min(len(sorted_ms) - 1, int(round(0.99 * (len(sorted_ms) - 1))))]
@@ -724,7 +823,12 @@ def run_gpu(args, rank, world, local_rank):
                                                  torch.cuda.get_device_properties(dev).multi_processor_count)},
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "four full steps (both transforms of the 8192x8192 discs "
-                                       f"mask each), single-threaded C oracle, {cpu_s:.1f} s"},
+                                       f"mask each), single-threaded C oracle, {cpu_s:.1f} s",
+                             "host_cores": os.cpu_count(),
+                             "all_cores": None if allc is None else {
+                                 "value": allc[0], "unit": UNIT, "cores": allc[2], "kind": "oracle",
+                                 "sample": "the same four full steps, the oracle's source built with "
+                                           f"-fopenmp (columns, then rows, over all cores), {allc[1]:.1f} s"}},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": H * W,
                     "d2h_bytes_per_step": 2 * 2 * 4 * H * W, "steps": e2e_steps,
                     "api": "edt_feature_pair_host, pinned host buffers",

@@ -153,25 +153,53 @@ typedef struct {
 typedef struct edt_plan edt_plan;
 
 /* A batch plan owns the device scratch, a device job table and the CUDA graph
- * that run up to n_max 2-D jobs (width <= 2048) in one replay.  `max_pixels`
- * bounds the total pixel count of one batch (scratch, about 0.26 bytes per
- * pixel, is sized from it).  Not thread-safe: use one plan from one thread
- * and one stream; plan creation allocates and may synchronise. */
+ * that run up to n_max jobs in one replay: 2-D jobs of any width edt_feature
+ * accepts and 3-D jobs whose y and x lines fit the batched 3-D kernels'
+ * shared memory (height up to about 1536, row width up to about 780; larger
+ * volumes: edt_feature).  `max_pixels` sizes the column-pass scratch the plan
+ * allocates up front (about 0.26 bytes per pixel of 2-D jobs up to 2048 wide);
+ * a batch that needs more grows it, which allocates and waits for the plan's
+ * earlier batches.  Not thread-safe: use one plan from one thread and one
+ * stream; plan creation allocates and may synchronise.  (Sec. 3: every job is
+ * the same column pass and envelope passes as edt_feature.) */
 edt_status edt_plan_create(edt_plan **plan, int n_max, int64_t max_pixels);
 edt_status edt_plan_destroy(edt_plan *plan);
 
-/* Run n 2-D jobs (n <= n_max) as one graph replay on `stream`: the job table
- * is copied to the device and two persistent kernels cover every job (column
- * pass, then row pass).  Results are bit-identical to n separate edt_feature
- * calls.  Returns after enqueueing; the host may then reuse `jobs`. */
+/* Run n jobs (n <= n_max; 2-D and 3-D mixed; pointers are device memory, F
+ * required) as one graph replay on `stream`: the job table is copied to the
+ * device and persistent kernels cover every job, one phase after the other
+ * (column pass of all jobs, 2-D row passes, 3-D y passes, 3-D x passes).
+ * Results are bit-identical to n separate edt_feature calls.  Returns after
+ * enqueueing; the host may then reuse `jobs`.  EDT_ERR_TOO_LARGE for a 3-D
+ * job the batch does not cover, EDT_ERR_INVALID for n > n_max or a NULL mask
+ * or F. */
 edt_status edt_batch(edt_plan *plan, const edt_job *jobs, int n,
                      edt_stream_t stream);
 
+/* Autotuning of the batch geometry.  Times, for each shape class (the
+ * rounded-up log2 of each side) among `jobs`, the candidate geometries of the
+ * batch kernels on those jobs -- narrow 2-D jobs: the smallest row segment,
+ * 2^8, 2^7 or 2^6 columns; 3-D jobs: 64, 32 or 128 positions per warp for the
+ * y pass, then 32, 64 or 128 for the x pass -- and keeps the fastest in the
+ * process-wide table that every later batch uses (saved and loaded with
+ * edt_tune_save / edt_tune_load).  Rows wider than 2048 have no knob.  Runs
+ * the jobs (device pointers, as edt_batch) several times on `stream`, which
+ * overwrites their outputs with the same bits; synchronous.  Results never
+ * depend on the choice. */
+edt_status edt_autotune_batch(edt_plan *plan, const edt_job *jobs, int n,
+                              edt_stream_t stream);
+/* The batch geometry in the table for a shape: values[0] = smallest row
+ * segment log2 (0 = built-in 8), values[1] / values[2] = y / x positions per
+ * warp (0 = built-in 64 / 32). */
+edt_status edt_batch_tune_get(int ndim, const int *shape, int *values);
+
 /* Continuous-batching server.  Jobs carry HOST pointers (mask in, D/F/dist
  * out).  A scheduler thread admits jobs while their device footprint fits
- * mem_budget_bytes, copies them in, groups the admitted jobs into batches,
- * runs them on n_streams streams so that batches overlap, copies results out
- * and completes the ticket.  Each result is identical to a plain edt_feature
+ * mem_budget_bytes, copies them in, groups the admitted jobs into batches
+ * (edt_batch's kernels; 3-D volumes beyond the batch limits run as plain
+ * transforms), runs them on n_streams streams so that batches overlap, copies
+ * results out and completes the ticket once the device has finished, with
+ * the device's status (a GPU error after enqueueing fails the ticket).  Each result is identical to a plain edt_feature
  * call on the same mask.  The budget is taken from the device when the
  * server is created (a memory pool of its own, grown to the budget less the
  * batch plans' scratch) and given back by edt_serve_destroy; EDT_ERR_BUDGET
@@ -190,6 +218,11 @@ edt_status edt_serve_submit(edt_server *server, const edt_job *job,
  * job failed.  A finished ticket is forgotten after it was reported once. */
 edt_status edt_serve_poll(edt_server *server, uint64_t ticket,
                           double *latency_s);
+/* edt_serve_poll that also reports wait_s, the seconds from submission to
+ * admission to a stream (latency_s - wait_s is the time on the stream:
+ * copies, transform, copies back).  Either pointer may be NULL. */
+edt_status edt_serve_poll_detail(edt_server *server, uint64_t ticket,
+                                 double *latency_s, double *wait_s);
 /* Wait until every submitted job has finished, then stop the scheduler and
  * free everything. */
 edt_status edt_serve_destroy(edt_server *server);
@@ -231,8 +264,8 @@ edt_status edt_feature2d_noalloc(const uint8_t *mask, int H, int W, int mode,
  * y pass: 8, 4, 16, 32, then x pass: 32, 16, 8) on `mask` (DEVICE, the given
  * shape and mode) and keeps the fastest for the shape's class -- the
  * rounded-up log2 of each side -- in a process-wide table that every later
- * call of that class uses (plain, pair and host-buffer calls; batches keep
- * their own rule).  Results do not depend on the choice: D and F are the same
+ * call of that class uses (plain, pair and host-buffer calls; batches are
+ * tuned by edt_autotune_batch).  Results do not depend on the choice: D and F are the same
  * bits for every candidate.  Synchronous; device scratch from the stream's
  * pool.  Without tuning, the built-in rule applies (16, 8, 32). */
 edt_status edt_autotune(const uint8_t *mask, int ndim, const int *shape,
@@ -243,7 +276,9 @@ edt_status edt_autotune(const uint8_t *mask, int ndim, const int *shape,
 edt_status edt_tune_get(int ndim, const int *shape, int *warps);
 /* Write the table to a text file / merge a file into the table (lines of
  * "ndim log2(side0) log2(side1) log2(side2) rows2d ypass xpass", '#' starts
- * a comment; warp counts are powers of two up to 16, 32, 32, or 0).
+ * a comment; warp counts are powers of two up to 16, 32, 32, or 0; batch
+ * geometry lines "b ndim log2(side0) log2(side1) log2(side2) lgmin ypos
+ * xpos" with lgmin 0 or 6..8 and positions 0, 32, 64 or 128).
  * Host-only; EDT_ERR_INVALID for unreadable or malformed files (the table is
  * then unchanged). */
 edt_status edt_tune_save(const char *path);

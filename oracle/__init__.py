@@ -33,21 +33,70 @@ _SRC = os.path.join(_HERE, "edt_oracle.c")
 _SRC_NEDT = os.path.join(_HERE, "nedt_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle_edt.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_edt_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
+
+
+def _compile(path, extra, required):
+    os.makedirs(_BUILD, exist_ok=True)
+    if (os.path.exists(path)
+            and os.path.getmtime(path) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_NEDT))):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-Wno-unknown-pragmas", "-shared", "-fPIC"] + extra + [_SRC, _SRC_NEDT, "-o", tmp, "-lm"]
+    if required:
+        subprocess.check_call(cmd)
+    elif subprocess.run(cmd, capture_output=True).returncode != 0:
+        return None
+    os.replace(tmp, path)
+    return path
 
 
 def build(force: bool = False) -> str:
-    """Compile edt_oracle.c into a shared library (plain gcc, no CUDA)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_NEDT))):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                           _SRC, _SRC_NEDT, "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    """Compile edt_oracle.c into a shared library (plain gcc, no CUDA): the
+    single-threaded checker, and (when gcc has OpenMP) the same source with
+    -fopenmp for the all-core CPU baseline timing."""
+    if force:
+        for p in (_LIB_PATH, _LIB_OMP_PATH):
+            if os.path.exists(p):
+                os.remove(p)
+    _compile(_LIB_OMP_PATH, ["-fopenmp"], required=False)
+    return _compile(_LIB_PATH, [], required=True)
+
+
+def edt_all_cores(mask, mode: int = TO_OBJECT):
+    """The same 2-D/3-D transform from the OpenMP build of the same source
+    (columns and rows spread over all host cores), for CPU baseline timing.
+    Returns (D, F, threads), or None when gcc has no OpenMP."""
+    path = _compile(_LIB_OMP_PATH, ["-fopenmp"], required=False)
+    if path is None:
+        return None
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            lib = ctypes.CDLL(path)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            lib.oracle_edt2d.restype = ctypes.c_int
+            lib.oracle_edt2d.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p]
+            lib.oracle_edt3d.restype = ctypes.c_int
+            lib.oracle_edt3d.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p]
+            _lib_omp = lib
+    m = _mask(mask)
+    D = np.empty(m.shape, dtype=np.int32)
+    F = np.empty(m.shape, dtype=np.int32)
+    if m.ndim == 2:
+        rc = _lib_omp.oracle_edt2d(_ptr(m, ctypes.c_uint8), m.shape[0], m.shape[1], int(mode),
+                                   _ptr(D, ctypes.c_int32), _ptr(F, ctypes.c_int32))
+    else:
+        rc = _lib_omp.oracle_edt3d(_ptr(m, ctypes.c_uint8), *m.shape, int(mode), _ptr(D, ctypes.c_int32),
+                                   _ptr(F, ctypes.c_int32))
+    if rc != 0:
+        raise MemoryError("oracle ran out of memory")
+    threads = int(os.environ.get("OMP_NUM_THREADS", 0)) or (os.cpu_count() or 1)
+    return D, F, threads
 
 
 def _load():

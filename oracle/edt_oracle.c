@@ -254,7 +254,11 @@ static void envelope_pass(int64_t *d, int32_t *feat, long n, long stride,
 
 /* 2-D EEDT of an M x L image (Sec. 3.1 column distances, then the Sec. 3.3.1
  * envelope per row).  D and F are M*L int32 arrays; F may be NULL.
- * Returns 0, or -1 when memory runs out. */
+ * Returns 0, or -1 when memory runs out.  Columns, and then rows, are
+ * independent of one another: built with -fopenmp (the all-core timing
+ * build only; the checker is built without it and runs this single-threaded)
+ * each thread takes whole columns, then whole rows, with its own line
+ * buffers; the arithmetic is the same. */
 int oracle_edt2d(const uint8_t *mask, int M, int L, int mode, int32_t *D,
                  int32_t *F)
 {
@@ -263,25 +267,39 @@ int oracle_edt2d(const uint8_t *mask, int M, int L, int mode, int32_t *D,
     int64_t max_dist = oracle_max_dist(2, shape);
     int64_t *d = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int32_t *feat = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-    line_work w;
-    int rc = work_alloc(&w, L > M ? L : M);
-    if (!d || !feat || rc != 0) {
-        rc = -1;
-        goto done;
+    int rc = 0;
+    if (!d || !feat) {
+        free(d); free(feat);
+        return -1;
     }
     init_sources(mask, n, mode, max_dist, d, feat);
-    for (long j = 0; j < L; ++j)
-        column_nearest(d + j, feat + j, M, L, 0, w.above);
-    for (long i = 0; i < M; ++i)
-        envelope_pass(d + i * L, feat + i * L, L, 1, max_dist, &w);
-    finish(d, feat, n, max_dist, D, F);
-done:
-    free(d); free(feat); work_free(&w);
+#pragma omp parallel
+    {
+        line_work w;
+        const int ok = work_alloc(&w, L > M ? L : M) == 0;
+        if (!ok) {
+#pragma omp atomic write
+            rc = -1;
+        }
+#pragma omp for schedule(static)
+        for (long j = 0; j < L; ++j)
+            if (ok)
+                column_nearest(d + j, feat + j, M, L, 0, w.above);
+#pragma omp for schedule(dynamic, 8)
+        for (long i = 0; i < M; ++i)
+            if (ok)
+                envelope_pass(d + i * L, feat + i * L, L, 1, max_dist, &w);
+        work_free(&w);
+    }
+    if (rc == 0)
+        finish(d, feat, n, max_dist, D, F);
+    free(d); free(feat);
     return rc;
 }
 
 /* 3-D EEDT of a Dz x H x W volume: the column distances of Sec. 3.1 along z,
- * then the envelope of Sec. 3.3.1 along y and along x. */
+ * then the envelope of Sec. 3.3.1 along y and along x (lines independent, as
+ * in 2-D). */
 int oracle_edt3d(const uint8_t *mask, int Dz, int H, int W, int mode,
                  int32_t *D, int32_t *F)
 {
@@ -294,26 +312,38 @@ int oracle_edt3d(const uint8_t *mask, int Dz, int H, int W, int mode,
     if (W > line) line = W;
     int64_t *d = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int32_t *feat = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-    line_work w;
-    int rc = work_alloc(&w, line);
-    if (!d || !feat || rc != 0) {
-        rc = -1;
-        goto done;
+    int rc = 0;
+    if (!d || !feat) {
+        free(d); free(feat);
+        return -1;
     }
     init_sources(mask, n, mode, max_dist, d, feat);
-    for (long p = 0; p < plane; ++p)
-        column_nearest(d + p, feat + p, Dz, plane, 0, w.above);
-    for (long z = 0; z < Dz; ++z)
-        for (long x = 0; x < W; ++x)
-            envelope_pass(d + z * plane + x, feat + z * plane + x, H, W,
-                          max_dist, &w);
-    for (long z = 0; z < Dz; ++z)
-        for (long y = 0; y < H; ++y)
-            envelope_pass(d + z * plane + y * W, feat + z * plane + y * W, W,
-                          1, max_dist, &w);
-    finish(d, feat, n, max_dist, D, F);
-done:
-    free(d); free(feat); work_free(&w);
+#pragma omp parallel
+    {
+        line_work w;
+        const int ok = work_alloc(&w, line) == 0;
+        if (!ok) {
+#pragma omp atomic write
+            rc = -1;
+        }
+#pragma omp for schedule(static)
+        for (long p = 0; p < plane; ++p)
+            if (ok)
+                column_nearest(d + p, feat + p, Dz, plane, 0, w.above);
+#pragma omp for schedule(dynamic, 8)
+        for (long zx = 0; zx < (long)Dz * W; ++zx)
+            if (ok)
+                envelope_pass(d + (zx / W) * plane + zx % W, feat + (zx / W) * plane + zx % W, H, W,
+                              max_dist, &w);
+#pragma omp for schedule(dynamic, 8)
+        for (long zy = 0; zy < (long)Dz * H; ++zy)
+            if (ok)
+                envelope_pass(d + zy * W, feat + zy * W, W, 1, max_dist, &w);
+        work_free(&w);
+    }
+    if (rc == 0)
+        finish(d, feat, n, max_dist, D, F);
+    free(d); free(feat);
     return rc;
 }
 

@@ -75,28 +75,29 @@ struct OutY {
     }
 };
 
-static size_t ypass_smem(int H, int lg, int NW)
+__host__ __device__ static inline size_t ypass_smem(int H, int lg, int NW)
 {
     return (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
-// One block: one z, 32 consecutive x (one line per lane), warps = y segments.
-__global__ void __launch_bounds__(1024)
-k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
+size_t batch_ypass_group_bytes(int H, int lg, int NW) { return ypass_smem(H, lg, NW); }
+
+// One y-pass tile: plane z, the 32 columns x0 .. x0+31 (one line per lane),
+// NW warps = y segments.  Run by the nthr threads of one engine (tid = thread
+// within it, warp = warp within it) over the shared memory at `base`.
+template <class Sync>
+__device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, uint32_t* __restrict__ P,
+                           int z, int x0, unsigned char* base, int tid, int nthr, int warp, Sync sync)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    short* gz = reinterpret_cast<short*>(smem);
-    const BandSmem sm = carve_band_smem(smem + (((size_t)H * 32 * 2 + 15) & ~size_t(15)), NW,
+    short* gz = reinterpret_cast<short*>(base);
+    const BandSmem sm = carve_band_smem(base + (((size_t)H * 32 * 2 + 15) & ~size_t(15)), NW,
                                         (1 << lg) >> 5);
-    const int lane = threadIdx.x & 31;
-    const int xtiles = (W + 31) / 32;
-    const int z = blockIdx.x / xtiles;
-    const int x0 = (blockIdx.x % xtiles) * 32;
+    const int lane = tid & 31;
     const int64_t plane = (int64_t)H * W;
     const int zb = z >> 5, zr = z & 31, zG = zb >> s.gs;
 
     // nearest source along z of every (y, x) of the tile
-    for (int e = threadIdx.x; e < H * 32; e += blockDim.x) {
+    for (int e = tid; e < H * 32; e += nthr) {
         const int y = e >> 5, xl = e & 31, x = x0 + xl;
         int g = -1;
         if (x < W) {
@@ -113,11 +114,22 @@ k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
         }
         gz[e] = (short)g;
     }
-    __syncthreads();
+    sync();
 
     const LineY line{gz, lane, z};
     const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
-    band_envelope(line, out, sm, H, lg, NW, nullptr);
+    band_envelope(line, out, sm, H, lg, NW, nullptr, warp, sync);
+}
+
+// One block: one z, 32 consecutive x (one line per lane), warps = y segments.
+__global__ void __launch_bounds__(1024)
+k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int xtiles = (W + 31) / 32;
+    const int z = blockIdx.x / xtiles;
+    const int x0 = (blockIdx.x % xtiles) * 32;
+    ypass_tile(H, W, s, lg, NW, P, z, x0, smem, threadIdx.x, blockDim.x, threadIdx.x >> 5, BlockSync());
 }
 
 // --- x pass ----------------------------------------------------------------
@@ -163,35 +175,35 @@ struct LineX {
     __device__ __forceinline__ int self_feature(int k) const { return (z * H + y) * W + k; }
 };
 
-static int xpass_pitch(int W) { return W | 1; }
+__host__ __device__ static inline int xpass_pitch(int W) { return W | 1; }
 
-static size_t xpass_smem(int W, int lg, int NW)
+__host__ __device__ static inline size_t xpass_smem(int W, int lg, int NW)
 {
     return (((size_t)32 * xpass_pitch(W) * 4 + 15) & ~size_t(15)) +
            band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
-// One block: 32 consecutive rows (z, y) of the volume (one per lane), warps =
-// x segments.
-__global__ void __launch_bounds__(1024)
-k_xpass3d(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D,
-          int32_t* F, float* dist)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int pitch = W | 1;
-    uint32_t* rec = reinterpret_cast<uint32_t*>(smem);   // [32][pitch]
-    const BandSmem sm = carve_band_smem(smem + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)), NW,
-                                        (1 << lg) >> 5);
-    const int lane = threadIdx.x & 31;
-    const int64_t nrows = (int64_t)Dz * H;
-    const int64_t row0 = (int64_t)blockIdx.x * 32;
+size_t batch_xpass_group_bytes(int W, int lg, int NW) { return xpass_smem(W, lg, NW); }
 
-    for (int e = threadIdx.x; e < 32 * W; e += blockDim.x) {
+// One x-pass unit: the 32 rows (z, y) starting at row0 of the Dz*H rows (one
+// per lane), NW warps = x segments; run by one engine as ypass_tile.
+template <class Sync>
+__device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D, int32_t* F,
+                           float* dist, int64_t row0, unsigned char* base, int tid, int nthr, int warp, Sync sync)
+{
+    const int pitch = W | 1;
+    uint32_t* rec = reinterpret_cast<uint32_t*>(base);   // [32][pitch]
+    const BandSmem sm = carve_band_smem(base + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)), NW,
+                                        (1 << lg) >> 5);
+    const int lane = tid & 31;
+    const int64_t nrows = (int64_t)Dz * H;
+
+    for (int e = tid; e < 32 * W; e += nthr) {
         const int rl = e / W, k = e - rl * W;
         const int64_t row = row0 + rl;
         rec[rl * pitch + k] = (row < nrows) ? P[row * W + k] : PNONE;
     }
-    __syncthreads();
+    sync();
 
     const int64_t row = row0 + lane;
     LineX line;
@@ -204,7 +216,135 @@ k_xpass3d(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D,
     line.self = ((uint32_t)line.z << 16) | (uint32_t)line.y;
     const int vec = row_vec_width(W, D, F, dist);
     const RowOut out{D, F, dist, row * W, row < nrows, vec};
-    band_envelope(line, out, sm, W, lg, NW, nullptr);
+    band_envelope(line, out, sm, W, lg, NW, nullptr, warp, sync);
+}
+
+// One block: 32 consecutive rows (z, y) of the volume (one per lane), warps =
+// x segments.
+__global__ void __launch_bounds__(1024)
+k_xpass3d(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D,
+          int32_t* F, float* dist)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    xpass_rows(Dz, H, W, lg, NW, P, D, F, dist, (int64_t)blockIdx.x * 32, smem, threadIdx.x, blockDim.x,
+               threadIdx.x >> 5, BlockSync());
+}
+
+// --- batched 3-D passes ------------------------------------------------------
+
+// Engine geometry of a 3-D line of n positions aiming at `pos` positions per
+// warp (at most BATCH_3D_WARPS warps, segments of at least 32 positions).
+void batch_line_geometry(int n, int pos, int& lg, int& NW)
+{
+    int want = (n + pos - 1) / pos;
+    if (want < 1) want = 1;
+    if (want > BATCH_3D_WARPS) want = BATCH_3D_WARPS;
+    lg = band_seg_log2(n, want);
+    NW = (n + (1 << lg) - 1) >> lg;
+}
+
+// Persistent y pass over every 3-D job of a batch: a work item is `groups`
+// consecutive (z, x-tile) units of one job, one engine of NW warps each.
+__global__ void __launch_bounds__(BATCH_3D_WARPS * 32)
+k_batch_ypass3d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = hdr->k_total[PH_Y];
+    unsigned* work = hdr->cnt + PH_Y;
+    const int nj = hdr->njobs;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(work, 1u);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].k_first[PH_Y] <= item) lo = mid; else hi = mid - 1;
+        }
+        const BatchJob& J = jobs[lo];
+        const int NW = J.NW;
+        const int grp = warp / NW, wg = warp - grp * NW;
+        const int xtiles = (J.W + 31) / 32;
+        const int64_t unit = (item - J.k_first[PH_Y]) * J.groups + grp;
+        if (grp < J.groups && unit < (int64_t)J.Dz * xtiles) {
+            unsigned char* base = smem + (size_t)grp * ypass_smem(J.H, J.lg, NW);
+            ypass_tile(J.H, J.W, J.s, J.lg, NW, reinterpret_cast<uint32_t*>(J.F), (int)(unit / xtiles),
+                       (int)(unit % xtiles) * 32, base, wg * 32 + lane, NW * 32, wg, GroupSync{1 + grp, NW * 32});
+        }
+        __syncthreads();
+    }
+}
+
+// Persistent x pass over every 3-D job of a batch: a work item is `xgroups`
+// consecutive 32-row units of one job.
+__global__ void __launch_bounds__(BATCH_3D_WARPS * 32)
+k_batch_xpass3d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = hdr->k_total[PH_X];
+    unsigned* work = hdr->cnt + PH_X;
+    const int nj = hdr->njobs;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(work, 1u);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].k_first[PH_X] <= item) lo = mid; else hi = mid - 1;
+        }
+        const BatchJob& J = jobs[lo];
+        const int NW = J.xNW;
+        const int grp = warp / NW, wg = warp - grp * NW;
+        const int64_t units = ((int64_t)J.Dz * J.H + 31) / 32;
+        const int64_t unit = (item - J.k_first[PH_X]) * J.xgroups + grp;
+        if (grp < J.xgroups && unit < units) {
+            unsigned char* base = smem + (size_t)grp * xpass_smem(J.W, J.xlg, NW);
+            xpass_rows(J.Dz, J.H, J.W, J.xlg, NW, reinterpret_cast<const uint32_t*>(J.F), J.D, J.F, J.dist,
+                       unit * 32, base, wg * 32 + lane, NW * 32, wg, GroupSync{1 + grp, NW * 32});
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_batch_ypass3d(const BatchHeader* hdr, const BatchJob* jobs, int blocks, cudaStream_t stream)
+{
+    k_batch_ypass3d<<<blocks, BATCH_3D_WARPS * 32, BATCH_3D_SMEM, stream>>>(hdr, jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_xpass3d(const BatchHeader* hdr, const BatchJob* jobs, int blocks, cudaStream_t stream)
+{
+    k_batch_xpass3d<<<blocks, BATCH_3D_WARPS * 32, BATCH_3D_SMEM, stream>>>(hdr, jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t set_batch_3d_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_batch_ypass3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BATCH_3D_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_batch_xpass3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_3D_SMEM);
+}
+
+int batch_3d_blocks_per_sm()
+{
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch_ypass3d, BATCH_3D_WARPS * 32, BATCH_3D_SMEM) !=
+            cudaSuccess || a < 1)
+        a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_xpass3d, BATCH_3D_WARPS * 32, BATCH_3D_SMEM) !=
+            cudaSuccess || b < 1)
+        b = 1;
+    return a < b ? a : b;
 }
 
 // Segments for lines of n positions: at most max_nw warps, fewer while the

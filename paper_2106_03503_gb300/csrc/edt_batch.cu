@@ -1,15 +1,18 @@
-// Batched 2-D transforms (edt_plan_create / edt_batch / edt_plan_destroy).
+// Batched transforms (edt_plan_create / edt_batch / edt_plan_destroy).
 //
 // A plan owns: the device scratch of the column pass for all jobs of a batch,
-// the arrival counters (one contiguous block, cleared by one memset), a device
-// job table, two pinned host copies of that table and two CUDA graphs.  Each
-// graph is [copy table host->device, clear counters, persistent column-pass
-// kernel, persistent row-pass kernel]; the kernels read the job count and all
-// per-job geometry from the table, so one instantiated graph serves every
-// batch.  edt_batch fills a pinned table (jobs sorted widest first, so that
-// the row pass hands out the most expensive work items first) and replays the
-// graph on the caller's stream; the two tables alternate so that the host can
-// prepare batch n+1 while batch n still copies.
+// the work and arrival counters, a device job table, two pinned host copies of
+// that table and two CUDA graphs.  Each graph is
+//   [copy table host->device, clear counters, column pass, 2-D row pass,
+//    wide 2-D row pass, 3-D y pass, 3-D x pass],
+// every kernel persistent (a fixed grid that takes work items from the
+// table), so one instantiated graph serves every batch: 2-D jobs of any
+// accepted width and 3-D jobs, mixed.  The kernels find the counters and the
+// job count through the table, so the scratch and counters may be
+// reallocated between batches without touching the graph.  edt_batch fills a
+// pinned table (edt_batch_table.cu) and replays the graph on the caller's
+// stream; the two tables alternate so that the host can prepare batch n+1
+// while batch n still copies.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -22,6 +25,13 @@ edt_status cuda_fail(cudaError_t e, const char* what);
 void clear_error();
 edt_status device_setup(int* sm_count);
 edt_status check_shape(int ndim, const int* shape, int mode);
+
+cudaError_t set_batch_attributes()
+{
+    cudaError_t e = set_batch_row_attributes();
+    if (e != cudaSuccess) return e;
+    return set_batch_3d_attributes();
+}
 }  // namespace edt
 
 using namespace edt;
@@ -29,28 +39,18 @@ using namespace edt;
 struct edt_plan {
     int device = 0;
     int n_max = 0;
-    int64_t max_pixels = 0;
     int sm_count = 0;
     size_t scratch_bytes = 0;
-    size_t counter_words = 0;
+    int64_t cnt_words = 0;
     size_t table_bytes = 0;
     char* scratch = nullptr;          // device
-    unsigned* counters = nullptr;     // device: [0] row-pass work counter, then tiles
+    unsigned* cnt = nullptr;          // device: work counters, then arrival counters
     char* dtable = nullptr;           // device: BatchHeader + BatchJob[n_max]
     char* htable[2] = {nullptr, nullptr};   // pinned host copies
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     cudaEvent_t done[2] = {nullptr, nullptr};
     int next = 0;
 };
-
-static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// Bytes of column-pass scratch (without counters) of one H x W job.
-static size_t job_scratch_bytes(const ColGeom& g)
-{
-    const size_t c = (size_t)g.cols * 4;
-    return 2 * al256((size_t)g.nb * c) + 2 * al256((size_t)g.nG * c);
-}
 
 static void plan_free(edt_plan* p)
 {
@@ -61,7 +61,7 @@ static void plan_free(edt_plan* p)
         if (p->htable[b]) cudaFreeHost(p->htable[b]);
     }
     if (p->scratch) cudaFree(p->scratch);
-    if (p->counters) cudaFree(p->counters);
+    if (p->cnt) cudaFree(p->cnt);
     if (p->dtable) cudaFree(p->dtable);
     delete p;
 }
@@ -79,14 +79,15 @@ extern "C" edt_status edt_plan_create(edt_plan** out, int n_max, int64_t max_pix
     edt_plan* p = new edt_plan();
     cudaGetDevice(&p->device);
     p->n_max = n_max;
-    p->max_pixels = max_pixels;
     p->sm_count = sms;
-    // per job at most (2*ceil(H/32) + 2*ceil(H/1024)) * W * 4 bytes + alignment
+    // enough for 2-D jobs up to BATCH_MAX_W wide totalling max_pixels (about
+    // 0.26 B/pixel, plus the rounding of each job to whole bands); a batch
+    // that needs more grows it
     p->scratch_bytes = (size_t)(0.26 * (double)max_pixels) + (size_t)n_max * (16 * BATCH_MAX_W + 1024);
-    p->counter_words = 1 + (size_t)n_max * ((BATCH_MAX_W + 31) / 32);
+    p->cnt_words = PH_COUNT + (int64_t)n_max * ((BATCH_MAX_W + 31) / 32);
     p->table_bytes = sizeof(BatchHeader) + (size_t)n_max * sizeof(BatchJob);
     if ((e = cudaMalloc(&p->scratch, p->scratch_bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&p->counters, p->counter_words * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&p->cnt, (size_t)p->cnt_words * 4)) != cudaSuccess ||
         (e = cudaMalloc(&p->dtable, p->table_bytes)) != cudaSuccess) {
         plan_free(p);
         return cuda_fail(e, "cudaMalloc (batch plan)");
@@ -100,6 +101,8 @@ extern "C" edt_status edt_plan_create(edt_plan** out, int n_max, int64_t max_pix
     const auto* jobs = reinterpret_cast<const BatchJob*>(p->dtable + sizeof(BatchHeader));
     const int k1_blocks = sms * batch_colbits_blocks_per_sm();
     const int k2_blocks = sms * batch_rows_blocks_per_sm();
+    const int kw_blocks = sms * batch_wide_blocks_per_sm();
+    const int k3_blocks = sms * batch_3d_blocks_per_sm();
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         if ((e = cudaMallocHost(&p->htable[b], p->table_bytes)) != cudaSuccess) break;
         memset(p->htable[b], 0, p->table_bytes);
@@ -107,9 +110,12 @@ extern "C" edt_status edt_plan_create(edt_plan** out, int n_max, int64_t max_pix
         cudaGraph_t graph = nullptr;
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
         cudaMemcpyAsync(p->dtable, p->htable[b], p->table_bytes, cudaMemcpyHostToDevice, cs);
-        cudaMemsetAsync(p->counters, 0, p->counter_words * 4, cs);
+        launch_batch_clear(hdr, sms * 2, cs);
         launch_batch_colbits(hdr, jobs, k1_blocks, cs);
-        launch_batch_rows2d(hdr, jobs, p->counters, k2_blocks, cs);
+        launch_batch_rows2d(hdr, jobs, k2_blocks, cs);
+        launch_batch_wide(hdr, jobs, kw_blocks, cs);
+        launch_batch_ypass3d(hdr, jobs, k3_blocks, cs);
+        launch_batch_xpass3d(hdr, jobs, k3_blocks, cs);
         e = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess) break;
         e = cudaGraphInstantiate(&p->exec[b], graph, 0);
@@ -134,80 +140,82 @@ extern "C" edt_status edt_plan_destroy(edt_plan* p)
     return EDT_OK;
 }
 
+// Grow the plan's scratch or counters to what a batch needs (after the
+// plan's earlier batches have finished with them).
+static edt_status plan_reserve(edt_plan* p, size_t scratch_bytes, int64_t cnt_words)
+{
+    if (scratch_bytes <= p->scratch_bytes && cnt_words <= p->cnt_words) return EDT_OK;
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaEventSynchronize(p->done[b])) != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    if (scratch_bytes > p->scratch_bytes) {
+        const size_t want = std::max(scratch_bytes, p->scratch_bytes + p->scratch_bytes / 4);
+        cudaFree(p->scratch);
+        p->scratch = nullptr;
+        p->scratch_bytes = 0;
+        if ((e = cudaMalloc(&p->scratch, want)) != cudaSuccess) return cuda_fail(e, "cudaMalloc (batch scratch)");
+        p->scratch_bytes = want;
+    }
+    if (cnt_words > p->cnt_words) {
+        const int64_t want = std::max(cnt_words, p->cnt_words + p->cnt_words / 4);
+        cudaFree(p->cnt);
+        p->cnt = nullptr;
+        p->cnt_words = 0;
+        if ((e = cudaMalloc(&p->cnt, (size_t)want * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc (batch counters)");
+        p->cnt_words = want;
+    }
+    return EDT_OK;
+}
+
+// Validate a batch: every job a transform edt_feature accepts, of a shape the
+// batch kernels cover.
+static edt_status check_batch(const edt_job* jobs, int n)
+{
+    for (int i = 0; i < n; ++i) {
+        const edt_job& j = jobs[i];
+        edt_status st = check_shape(j.ndim, j.shape, j.mode);
+        if (st != EDT_OK) return st;
+        if (!j.mask || !j.F) return fail(EDT_ERR_INVALID, "batch job %d: mask and F must not be NULL", i);
+        const char* why = "";
+        if (batch_kind(j, &why) < 0) return fail(EDT_ERR_TOO_LARGE, "batch job %d: %s", i, why);
+    }
+    return EDT_OK;
+}
+
+namespace edt {
+
+// Enqueue a validated batch; scratch: the column-pass scratch to use (device,
+// at least batch_layout's bytes), or NULL for the plan's own.
+edt_status batch_enqueue(edt_plan* p, const edt_job* jobs, int n, char* scratch, cudaStream_t stream)
+{
+    size_t need = 0;
+    int64_t words = 0;
+    batch_layout(jobs, n, &need, &words);
+    edt_status st = plan_reserve(p, scratch ? 0 : need, words);
+    if (st != EDT_OK) return st;
+    const int b = p->next;
+    cudaError_t e = cudaEventSynchronize(p->done[b]);   // table b no longer being copied
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    auto* hdr = reinterpret_cast<BatchHeader*>(p->htable[b]);
+    auto* tab = reinterpret_cast<BatchJob*>(p->htable[b] + sizeof(BatchHeader));
+    batch_fill(jobs, n, scratch ? scratch : p->scratch, p->cnt, hdr, tab);
+    if ((e = cudaGraphLaunch(p->exec[b], stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    if ((e = cudaEventRecord(p->done[b], stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    p->next ^= 1;
+    return EDT_OK;
+}
+
+}  // namespace edt
+
 extern "C" edt_status edt_batch(edt_plan* p, const edt_job* jobs, int n, edt_stream_t stream)
 {
     if (!p) return fail(EDT_ERR_INVALID, "plan is NULL");
     if (n < 0 || n > p->n_max) return fail(EDT_ERR_INVALID, "batch of %d jobs exceeds the plan's %d", n, p->n_max);
     if (n == 0) return EDT_OK;
     if (!jobs) return fail(EDT_ERR_INVALID, "jobs is NULL");
-    int64_t px = 0;
-    for (int i = 0; i < n; ++i) {
-        const edt_job& j = jobs[i];
-        if (j.ndim != 2) return fail(EDT_ERR_INVALID, "batch job %d: only 2-D jobs are batched", i);
-        edt_status st = check_shape(2, j.shape, j.mode);
-        if (st != EDT_OK) return st;
-        if (j.shape[1] > BATCH_MAX_W)
-            return fail(EDT_ERR_TOO_LARGE, "batch job %d: width %d exceeds %d", i, j.shape[1], BATCH_MAX_W);
-        if (!j.mask || !j.F) return fail(EDT_ERR_INVALID, "batch job %d: mask and F must not be NULL", i);
-        px += (int64_t)j.shape[0] * j.shape[1];
-    }
-    if (px > p->max_pixels)
-        return fail(EDT_ERR_TOO_LARGE, "batch of %lld pixels exceeds the plan's %lld",
-                    (long long)px, (long long)p->max_pixels);
-
-    const int b = p->next;
-    cudaError_t e = cudaEventSynchronize(p->done[b]);   // table b no longer being copied
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-    // widest jobs first
-    std::vector<int> order(n);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-        return jobs[a].shape[1] > jobs[c].shape[1];
-    });
-    auto* hdr = reinterpret_cast<BatchHeader*>(p->htable[b]);
-    auto* tab = reinterpret_cast<BatchJob*>(p->htable[b] + sizeof(BatchHeader));
-    size_t off = 0, cnt_off = 1;
-    int64_t k1 = 0, k2 = 0;
-    for (int t = 0; t < n; ++t) {
-        const edt_job& j = jobs[order[t]];
-        BatchJob& J = tab[t];
-        const int H = j.shape[0], W = j.shape[1];
-        J.mask = j.mask;
-        J.D = j.D;
-        J.F = j.F;
-        J.dist = j.dist;
-        J.g = col_geom(H, W, true);
-        J.mode = j.mode;
-        J.vec = (W % 16 == 0) && ((reinterpret_cast<uintptr_t>(j.mask) & 15) == 0);
-        const size_t need = job_scratch_bytes(J.g);
-        if (off + need > p->scratch_bytes)
-            return fail(EDT_ERR_TOO_LARGE, "batch scratch exhausted at job %d", order[t]);
-        const size_t c = (size_t)W * 4;
-        char* base = p->scratch + off;
-        J.s.C = reinterpret_cast<uint32_t*>(base);
-        J.s.U = reinterpret_cast<uint32_t*>(base + al256((size_t)J.g.nb * c));
-        J.s.GFL = reinterpret_cast<uint32_t*>(base + 2 * al256((size_t)J.g.nb * c));
-        J.s.GAB = reinterpret_cast<uint32_t*>(base + 2 * al256((size_t)J.g.nb * c) + al256((size_t)J.g.nG * c));
-        J.s.cnt = p->counters + cnt_off;
-        J.s.gs = J.g.gs;
-        off += need;
-        cnt_off += (size_t)J.g.ntiles;
-        batch_row_geometry(W, J.lg, J.NW, J.groups);
-        J.pad0 = 0;
-        J.k1_first = k1;
-        J.k2_first = k2;
-        k1 += J.g.ntiles * (int64_t)J.g.nG;
-        k2 += (J.g.nb + J.groups - 1) / J.groups;
-    }
-    hdr->njobs = n;
-    hdr->pad0 = 0;
-    hdr->k1_total = k1;
-    hdr->k2_total = k2;
-    if ((e = cudaGraphLaunch(p->exec[b], (cudaStream_t)stream)) != cudaSuccess)
-        return cuda_fail(e, "cudaGraphLaunch");
-    if ((e = cudaEventRecord(p->done[b], (cudaStream_t)stream)) != cudaSuccess)
-        return cuda_fail(e, "cudaEventRecord");
-    p->next ^= 1;
-    clear_error();
-    return EDT_OK;
+    edt_status st = check_batch(jobs, n);
+    if (st != EDT_OK) return st;
+    st = batch_enqueue(p, jobs, n, nullptr, (cudaStream_t)stream);
+    if (st == EDT_OK) clear_error();
+    return st;
 }

@@ -391,17 +391,17 @@ cudaError_t launch_colbits_sheared(const uint8_t* mask, const ColGeom& g, int mo
     return cudaGetLastError();
 }
 
-// Persistent column pass over every job of a batch: warp units are numbered
-// job by job (k1_first); every warp takes one contiguous range of them, so
-// that it finds its first job by binary search once and then steps from job
-// to job.
+// Persistent column pass over every job of a batch (for a 3-D job the z pass
+// over its Dz x H*W view): warp units are numbered job by job
+// (k_first[PH_COL]); every warp takes one contiguous range of them, so that it
+// finds its first job by binary search once and then steps from job to job.
 __global__ void __launch_bounds__(K1_WARPS * 32)
 k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs)
 {
     __shared__ uint32_t cw[K1_WARPS][32][32];
     __shared__ uint32_t upS[K1_WARPS][32][32];
     const int warp = threadIdx.x >> 5;
-    const int64_t total = hdr->k1_total;
+    const int64_t total = hdr->k_total[PH_COL];
     const int nj = hdr->njobs;
     const int64_t nw = (int64_t)gridDim.x * K1_WARPS, w = (int64_t)blockIdx.x * K1_WARPS + warp;
     const int64_t g0 = total * w / nw, g1 = total * (w + 1) / nw;
@@ -410,15 +410,15 @@ k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
         int hi = nj - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].k1_first <= g0) lo = mid; else hi = mid - 1;
+            if (jobs[mid].k_first[PH_COL] <= g0) lo = mid; else hi = mid - 1;
         }
     }
     for (int64_t gw = g0; gw < g1; ++gw) {
-        while (lo + 1 < nj && jobs[lo + 1].k1_first <= gw) ++lo;
+        while (lo + 1 < nj && jobs[lo + 1].k_first[PH_COL] <= gw) ++lo;
         const BatchJob& J = jobs[lo];
         const ColGeom g = J.g;
         const ColScratch s = J.s;
-        const int64_t local = gw - J.k1_first;
+        const int64_t local = gw - J.k_first[PH_COL];
         if (J.vec)
             colbits_warp<true, false, 0, true>(J.mask, g, J.mode, s, s, local % g.ntiles,
                                                (int)(local / g.ntiles), cw[warp], upS[warp]);
@@ -427,6 +427,22 @@ k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
                                                 (int)(local / g.ntiles), cw[warp], upS[warp]);
         __syncwarp();
     }
+}
+
+// Zero the batch's work and arrival counters (their number is in the table,
+// so the graph node does not depend on the batch).
+__global__ void __launch_bounds__(256) k_batch_clear(const BatchHeader* __restrict__ hdr)
+{
+    unsigned* c = hdr->cnt;
+    const int64_t n = hdr->cnt_words;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c[i] = 0u;
+}
+
+cudaError_t launch_batch_clear(const BatchHeader* hdr, int blocks, cudaStream_t stream)
+{
+    k_batch_clear<<<blocks, 256, 0, stream>>>(hdr);
+    return cudaGetLastError();
 }
 
 int batch_colbits_blocks_per_sm()

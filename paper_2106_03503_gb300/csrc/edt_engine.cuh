@@ -282,6 +282,18 @@ struct BlockSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
 
+// Barrier of one band engine of a block that runs several side by side:
+// named barrier `id` (1 + the engine's index; 0 is __syncthreads) over its
+// nthreads threads, or a warp barrier for a one-warp engine.
+struct GroupSync {
+    int id, nthreads;
+    __device__ __forceinline__ void operator()() const
+    {
+        if (nthreads <= 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+    }
+};
+
 // Cursor over the merged hull of this lane's line, moving right: the hull
 // word that holds the last returned member stays in a register.
 struct HullCursor {

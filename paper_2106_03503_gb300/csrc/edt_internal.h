@@ -77,43 +77,93 @@ cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
 cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,
                            int32_t* F, float* dist, cudaStream_t stream);
 
-// Batched 2-D transforms.  A device job table (header + jobs) drives two
-// persistent kernels: the column pass over every job's (tile, group) warps and
-// the row pass over every job's work items (`groups` bands per item, several
-// bands of a narrow image side by side in one block).
+// Batched transforms.  A device job table (header + jobs) drives persistent
+// kernels that each cover one phase of every job in the batch:
+//   clear    zero the work and arrival counters (their number is in the header)
+//   colbits  the column pass of every job (for 3-D the z pass over Dz x H*W)
+//   rows2d   2-D row pass, widths up to BATCH_MAX_W (several bands side by side)
+//   wide     2-D row pass, wider rows (one band per block)
+//   ypass    3-D y pass (several (z, x-tile) units side by side)
+//   xpass    3-D x pass (several 32-row units side by side)
+// Each phase numbers its work items job by job (k_first[phase]); a job of
+// another kind has none in that phase.
+enum BatchKind { BATCH_2D = 0, BATCH_2D_WIDE = 1, BATCH_3D = 2 };
+enum BatchPhase { PH_COL = 0, PH_ROWS = 1, PH_WIDE = 2, PH_Y = 3, PH_X = 4, PH_COUNT = 5 };
+
 struct BatchJob {
     const uint8_t* mask;
     int32_t* D;
     int32_t* F;
     float* dist;
     ColScratch s;
-    ColGeom g;             // rows = H, cols = W
-    int mode, vec;         // vec: 16-byte mask loads allowed
-    int lg, NW, groups;    // row pass: segment log2, warps per band, bands per item
-    int pad0;
-    int64_t k1_first;      // first column-pass warp of this job
-    int64_t k2_first;      // first row-pass work item of this job
+    ColGeom g;             // column pass: rows = H (2-D) or Dz (3-D), cols = W or H*W
+    int kind, mode, vec;   // vec: 16-byte mask loads allowed
+    int Dz, H, W;          // image shape (Dz = 1 for 2-D)
+    int lg, NW, groups;    // rows2d / wide / ypass: segment log2, warps per engine, engines per item
+    int xlg, xNW, xgroups; // xpass
+    int64_t k_first[PH_COUNT];   // first work item of this job in each phase
 };
 
 struct BatchHeader {
     int njobs;
     int pad0;
-    int64_t k1_total;
-    int64_t k2_total;
+    int64_t k_total[PH_COUNT];   // work items per phase
+    unsigned* cnt;               // [0, PH_COUNT): work counters; then arrival counters
+    int64_t cnt_words;           // words of cnt the clear kernel zeroes
 };
 
-constexpr int BATCH_MAX_W = 2048;      // widest image a batch accepts
+constexpr int BATCH_MAX_W = 2048;      // widest image of the rows2d phase
 constexpr int BATCH_K2_WARPS = 16;     // threads per row-pass block / 32
+constexpr int BATCH_3D_WARPS = 16;     // threads per y / x pass block / 32
+constexpr size_t BATCH_3D_SMEM = (size_t)108 << 10;   // dynamic shared memory of a y / x pass block
 int batch_colbits_blocks_per_sm();
 int batch_rows_blocks_per_sm();
+int batch_wide_blocks_per_sm();
+int batch_3d_blocks_per_sm();
 
-void batch_row_geometry(int W, int& lg, int& NW, int& groups);
+// Geometry overrides of the batch phases (edt_autotune_batch), 0 = built-in:
+// rows2d_lgmin = smallest segment log2 of the rows2d phase (built-in 8, i.e.
+// segments of at least 256 columns); y_pos / x_pos = positions per warp the
+// y / x pass aims at (built-in 64 / 32).
+struct BatchTuning {
+    int rows2d_lgmin = 0;
+    int y_pos = 0;
+    int x_pos = 0;
+};
+BatchTuning batch_tuning_lookup(int ndim, const int* shape);
+void batch_tuning_store(int ndim, const int* shape, const BatchTuning& t);
+
+void batch_row_geometry(int W, int lgmin, int& lg, int& NW, int& groups);
 size_t batch_rows_smem();
+size_t batch_wide_smem();
+// 3-D engine geometry of a line of n positions aiming at `pos` positions per
+// warp, and its shared memory per engine (y: H positions; x: W positions)
+void batch_line_geometry(int n, int pos, int& lg, int& NW);
+size_t batch_ypass_group_bytes(int H, int lg, int NW);
+size_t batch_xpass_group_bytes(int W, int lg, int NW);
+
+// Job table of one batch (edt_batch_table.cpp).  batch_kind: the job's kind,
+// or -1 when it cannot be batched (`why` then says so).  batch_layout: the
+// column-pass scratch bytes and counter words a batch needs.  batch_fill: the
+// table (jobs ordered by kind, the heaviest first within a kind), with the
+// scratch carved from `scratch` and the counters from `cnt` (device
+// addresses, at least batch_layout's sizes).  Shapes must have passed
+// check_shape and batch_kind.
+int batch_kind(const edt_job& j, const char** why);
+size_t batch_job_scratch_bytes(const edt_job& j);
+void batch_layout(const edt_job* jobs, int n, size_t* scratch_bytes, int64_t* cnt_words);
+void batch_fill(const edt_job* jobs, int n, char* scratch, unsigned* cnt, BatchHeader* hdr, BatchJob* tab);
+
+cudaError_t launch_batch_clear(const BatchHeader* hdr, int blocks, cudaStream_t stream);
 cudaError_t launch_batch_colbits(const BatchHeader* hdr, const BatchJob* jobs, int blocks,
                                  cudaStream_t stream);
-cudaError_t launch_batch_rows2d(const BatchHeader* hdr, const BatchJob* jobs, unsigned* work,
-                                int blocks, cudaStream_t stream);
+cudaError_t launch_batch_rows2d(const BatchHeader* hdr, const BatchJob* jobs, int blocks, cudaStream_t stream);
+cudaError_t launch_batch_wide(const BatchHeader* hdr, const BatchJob* jobs, int blocks, cudaStream_t stream);
+cudaError_t launch_batch_ypass3d(const BatchHeader* hdr, const BatchJob* jobs, int blocks, cudaStream_t stream);
+cudaError_t launch_batch_xpass3d(const BatchHeader* hdr, const BatchJob* jobs, int blocks, cudaStream_t stream);
 cudaError_t set_batch_attributes();
+cudaError_t set_batch_row_attributes();
+cudaError_t set_batch_3d_attributes();
 
 // Kernel tracing (see edt_trace_enable): trace_begin records the start event
 // of a launch on `stream` and returns a slot, trace_end its stop event.

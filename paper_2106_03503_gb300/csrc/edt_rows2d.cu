@@ -285,14 +285,15 @@ cudaError_t launch_rows2d_pair(int H, int W, const ColGeom& g, const ColScratch&
 
 // --- batched row pass -------------------------------------------------------
 
-// Row-pass geometry of a batch job of width W: segments of 2^lg columns (at
-// least 256: narrow images get fewer warps per band and more bands per block
-// instead of many short segments to merge), NW warps per band, `groups`
-// bands side by side in one 16-warp block.
-void batch_row_geometry(int W, int& lg, int& NW, int& groups)
+// Row-pass geometry of a batch job of width W <= BATCH_MAX_W: segments of
+// 2^lg columns (at least 2^lgmin, built-in 2^8: narrow images get fewer warps
+// per band and more bands per block instead of many short segments to merge),
+// NW warps per band, `groups` bands side by side in one 16-warp block.
+void batch_row_geometry(int W, int lgmin, int& lg, int& NW, int& groups)
 {
     lg = band_seg_log2(W, BATCH_K2_WARPS);
-    if (lg < 8) lg = 8;
+    const int lo = lgmin > 0 ? lgmin : 8;
+    if (lg < lo) lg = lo;
     NW = (W + (1 << lg) - 1) >> lg;
     groups = BATCH_K2_WARPS / NW;
 }
@@ -302,38 +303,43 @@ __host__ __device__ static size_t batch_group_bytes(int W, int lg, int NW)
     return band2d_col_bytes(W) + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
+// Segment minimums the autotuner may choose for the rows2d phase (the
+// kernel's shared memory covers every one of them).
+static const int kRowsLgmin[] = {6, 7, 8};
+
 size_t batch_rows_smem()
 {
     size_t mx = 0;
-    for (int W = 1; W <= BATCH_MAX_W; ++W) {
-        int lg, NW, groups;
-        batch_row_geometry(W, lg, NW, groups);
-        const size_t b = (size_t)groups * batch_group_bytes(W, lg, NW);
-        if (b > mx) mx = b;
-    }
+    for (int lgmin : kRowsLgmin)
+        for (int W = 1; W <= BATCH_MAX_W; ++W) {
+            int lg, NW, groups;
+            batch_row_geometry(W, lgmin, lg, NW, groups);
+            const size_t b = (size_t)groups * batch_group_bytes(W, lg, NW);
+            if (b > mx) mx = b;
+        }
     return mx;
 }
 
-// Barrier of one band engine inside a block that runs several: a warp barrier
-// for one-warp engines, else a named barrier (ids 1..8; 0 is __syncthreads).
-struct DynSync {
-    int id, nthreads;
-    __device__ __forceinline__ void operator()() const
-    {
-        if (nthreads <= 32) __syncwarp();
-        else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-    }
-};
+// Rows wider than BATCH_MAX_W: one band per block, up to 16 warps.
+size_t batch_wide_smem()
+{
+    const int W = 16384;
+    const int lg = band_seg_log2(W, BATCH_K2_WARPS);
+    return batch_group_bytes(W, lg, (W + (1 << lg) - 1) >> lg);
+}
 
-__global__ void __launch_bounds__(BATCH_K2_WARPS * 32, 2)
-k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs,
-               unsigned* __restrict__ work)
+// Persistent row pass of phase PH (PH_ROWS: 2-D jobs up to BATCH_MAX_W wide,
+// `groups` bands per work item; PH_WIDE: wider rows, one band per item).
+template <int PH>
+__global__ void __launch_bounds__(BATCH_K2_WARPS * 32, PH == PH_ROWS ? 2 : 1)
+k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t total = hdr->k2_total;
+    const int64_t total = hdr->k_total[PH];
+    unsigned* work = hdr->cnt + PH;
     const int nj = hdr->njobs;
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(work, 1u);
@@ -343,19 +349,19 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
         int lo = 0, hi = nj - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].k2_first <= item) lo = mid; else hi = mid - 1;
+            if (jobs[mid].k_first[PH] <= item) lo = mid; else hi = mid - 1;
         }
         const BatchJob& J = jobs[lo];
-        const int W = (int)J.g.cols, H = J.g.rows, lg = J.lg, NW = J.NW;
+        const int W = J.W, H = J.H, lg = J.lg, NW = J.NW;
         const int grp = warp / NW, wg = warp - grp * NW;
-        const int b = (int)((item - J.k2_first) * J.groups) + grp;
+        const int b = (int)((item - J.k_first[PH]) * J.groups) + grp;
         if (grp < J.groups && b < J.g.nb) {
             unsigned char* base = smem + (size_t)grp * batch_group_bytes(W, lg, NW);
             uint32_t* sbits = reinterpret_cast<uint32_t*>(base);
             uint32_t* supdn = sbits + W;
             unsigned char* sfull = reinterpret_cast<unsigned char*>(supdn + W);
             const BandSmem sm = carve_band_smem(base + band2d_col_bytes(W), NW, (1 << lg) >> 5);
-            const DynSync sync{1 + grp, NW * 32};
+            const GroupSync sync{1 + grp, NW * 32};
             stage_band(J.s, b, H, W, sbits, supdn, sfull, wg * 32 + lane, NW * 32);
             sync();
             BandRow2D line;
@@ -376,24 +382,41 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
     }
 }
 
-cudaError_t launch_batch_rows2d(const BatchHeader* hdr, const BatchJob* jobs, unsigned* work,
-                                int blocks, cudaStream_t stream)
+cudaError_t launch_batch_rows2d(const BatchHeader* hdr, const BatchJob* jobs, int blocks, cudaStream_t stream)
 {
-    k_batch_rows2d<<<blocks, BATCH_K2_WARPS * 32, batch_rows_smem(), stream>>>(hdr, jobs, work);
+    k_batch_rows2d<PH_ROWS><<<blocks, BATCH_K2_WARPS * 32, batch_rows_smem(), stream>>>(hdr, jobs);
     return cudaGetLastError();
 }
 
-cudaError_t set_batch_attributes()
+cudaError_t launch_batch_wide(const BatchHeader* hdr, const BatchJob* jobs, int blocks, cudaStream_t stream)
 {
-    return cudaFuncSetAttribute(k_batch_rows2d, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)batch_rows_smem());
+    k_batch_rows2d<PH_WIDE><<<blocks, BATCH_K2_WARPS * 32, batch_wide_smem(), stream>>>(hdr, jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t set_batch_row_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_batch_rows2d<PH_ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_rows_smem());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_batch_rows2d<PH_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)batch_wide_smem());
 }
 
 int batch_rows_blocks_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows2d, BATCH_K2_WARPS * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows2d<PH_ROWS>, BATCH_K2_WARPS * 32,
                                                       batch_rows_smem()) != cudaSuccess || n < 1)
+        n = 1;
+    return n;
+}
+
+int batch_wide_blocks_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows2d<PH_WIDE>, BATCH_K2_WARPS * 32,
+                                                      batch_wide_smem()) != cudaSuccess || n < 1)
         n = 1;
     return n;
 }

@@ -3,16 +3,19 @@
 // Jobs arrive with HOST buffers.  A scheduler thread keeps a FIFO of submitted
 // jobs and a set of CUDA streams, each owning a batch plan.  Whenever a stream
 // is idle and the head of the FIFO fits the device-memory budget, it admits
-// jobs in arrival order while they fit, allocates their device buffers from
-// the server's memory pool, and enqueues on that stream: the mask copies in,
-// one batched launch for the 2-D jobs a plan accepts (width <= 2048) and plain
-// transforms for the others (wider 2-D images, 3-D volumes), the result copies
-// out, the buffer frees, and a host callback that completes the tickets and
-// returns their bytes to the budget.  Batches on different streams overlap on
-// the device; requests that arrive while batches run are admitted as soon as
-// a stream and enough budget are free.  Every result is the same as a plain
-// edt_feature call on the same mask (the kernels do not depend on batch
-// membership), which the tests check alone and in the mix.
+// jobs in arrival order while they fit, allocates their device buffers (and
+// the batch's column-pass scratch) from the server's memory pool, and
+// enqueues on that stream: the mask copies in, batched replays for every job
+// the batch kernels cover (2-D of any width, 3-D volumes up to the batch
+// limits) and plain transforms for the rest (larger volumes), the result
+// copies out, the buffer frees, and an event.  A completion thread per stream
+// waits for that event and completes the tickets with the status the device
+// reports (an error raised by the GPU after enqueueing fails the tickets),
+// then returns their bytes to the budget.  Batches on different streams
+// overlap on the device; requests that arrive while batches run are admitted
+// as soon as a stream and enough budget are free.  Every result is the same as
+// a plain edt_feature call on the same mask (the kernels do not depend on
+// batch membership), which the tests check alone and in the mix.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -35,6 +38,7 @@ size_t scratch_bytes(int ndim, const int* shape);
 edt_status run_transform(const uint8_t* mask, int ndim, const int* shape, int mode,
                          int32_t* D, int32_t* F, float* dist, void* scratch,
                          int sm_count, cudaStream_t stream);
+edt_status batch_enqueue(edt_plan* p, const edt_job* jobs, int n, char* scratch, cudaStream_t stream);
 }  // namespace edt
 
 using namespace edt;
@@ -60,17 +64,26 @@ struct Pending {
 struct Ticket {
     int state = 0;           // 0 queued, 1 running, 2 done
     edt_status status = EDT_OK;
-    double latency = 0.0;
-    Clock::time_point t_submit;
+    double latency = 0.0;    // submission -> completion
+    double wait = 0.0;       // submission -> admission to a stream
+    Clock::time_point t_submit, t_admit;
 };
 
+struct Completion {
+    size_t bytes;
+    std::vector<uint64_t> tickets;
+    edt_status status;       // of the enqueueing
+};
+
+// One stream with its batch plan and the thread that completes its batches.
 struct StreamSlot {
     cudaStream_t stream = nullptr;
     edt_plan* plan = nullptr;
+    cudaEvent_t done = nullptr;
     bool busy = false;
+    Completion* pending = nullptr;   // enqueued, waiting for `done`
+    std::thread completer;
 };
-
-struct Completion;
 
 }  // namespace
 
@@ -81,7 +94,7 @@ struct edt_server {
     size_t budget = 0;       // bytes available to job buffers
     size_t in_use = 0;
     int64_t plan_pixels = 0;
-    std::vector<StreamSlot> slots;
+    std::vector<StreamSlot> slots;     // fixed once created (threads keep indices)
     std::deque<Pending> queue;
     std::unordered_map<uint64_t, Ticket> tickets;
     uint64_t next_ticket = 1;
@@ -94,37 +107,41 @@ struct edt_server {
 
 namespace {
 
-struct Completion {
-    edt_server* srv;
-    int slot;
-    size_t bytes;
-    std::vector<uint64_t> tickets;
-    edt_status status;
-};
-
-// Runs on a CUDA callback thread once the stream reached the end of a batch;
-// must not call CUDA.
-void CUDART_CB on_batch_done(void* arg)
+// Completion thread of stream slot `si`: waits for each enqueued batch's
+// event, then completes its tickets with the device's status and gives the
+// bytes back to the budget.
+void completer(edt_server* s, int si)
 {
-    Completion* c = static_cast<Completion*>(arg);
-    edt_server* s = c->srv;
-    const auto now = Clock::now();
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
+    cudaSetDevice(s->device);
+    StreamSlot& slot = s->slots[si];
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        s->cv.wait(lk, [&] { return slot.pending != nullptr || (s->stopping && !slot.busy); });
+        if (!slot.pending) break;
+        Completion* c = slot.pending;
+        lk.unlock();
+        const cudaError_t e = cudaEventSynchronize(slot.done);
+        edt_status status = c->status;
+        if (status == EDT_OK && e != cudaSuccess) status = EDT_ERR_CUDA;
+        const auto now = Clock::now();
+        lk.lock();
         for (uint64_t t : c->tickets) {
             auto it = s->tickets.find(t);
             if (it == s->tickets.end()) continue;
             it->second.state = 2;
-            it->second.status = c->status;
+            it->second.status = status;
             it->second.latency = std::chrono::duration<double>(now - it->second.t_submit).count();
         }
         s->in_use -= c->bytes;
         s->outstanding -= (int)c->tickets.size();
-        s->slots[c->slot].busy = false;
+        slot.pending = nullptr;
+        slot.busy = false;
+        delete c;
+        s->cv.notify_all();
     }
-    s->cv.notify_all();
-    delete c;
 }
+
+bool served_in_batch(const edt_job& j) { return batch_kind(j, nullptr) >= 0; }
 
 size_t job_bytes(const edt_job& j, int64_t n)
 {
@@ -132,7 +149,7 @@ size_t job_bytes(const edt_job& j, int64_t n)
     size_t b = al((size_t)n) + al((size_t)n * 4);           // mask, F
     if (j.D) b += al((size_t)n * 4);
     if (j.dist) b += al((size_t)n * 4);
-    b += scratch_bytes(j.ndim, j.shape);                     // column-pass scratch
+    b += al(served_in_batch(j) ? batch_job_scratch_bytes(j) : scratch_bytes(j.ndim, j.shape));   // column pass
     return b;
 }
 
@@ -158,8 +175,7 @@ void launch_batch(edt_server* s, int si, std::vector<Pending>& batch, size_t byt
         Dev d{};
         cudaError_t e = cudaSuccess;
         const size_t n = (size_t)p.n;
-        const bool batched = p.job.ndim == 2 && p.job.shape[1] <= BATCH_MAX_W &&
-                             (int64_t)n <= s->plan_pixels;
+        const bool batched = served_in_batch(p.job);
         if ((e = cudaMallocFromPoolAsync((void**)&d.mask, n, s->pool, st)) != cudaSuccess ||
             (e = cudaMallocFromPoolAsync((void**)&d.F, n * 4, s->pool, st)) != cudaSuccess ||
             (p.job.D && (e = cudaMallocFromPoolAsync((void**)&d.D, n * 4, s->pool, st)) != cudaSuccess) ||
@@ -187,19 +203,25 @@ void launch_batch(edt_server* s, int si, std::vector<Pending>& batch, size_t byt
                                    d.dist, d.scratch, s->sm_count, st);
         }
     }
-    // batched 2-D jobs: one or more plan replays
+    // batched jobs: one or more plan replays, each with its column-pass
+    // scratch from the pool (counted in the jobs' bytes)
+    std::vector<void*> bscratch;
     for (size_t off = 0; off < bj.size() && status == EDT_OK;) {
-        size_t cnt = 0;
-        int64_t px = 0;
-        while (off + cnt < bj.size() && cnt < (size_t)SERVE_PLAN_JOBS) {
-            const int64_t q = (int64_t)bj[off + cnt].shape[0] * bj[off + cnt].shape[1];
-            if (cnt > 0 && px + q > s->plan_pixels) break;
-            px += q;
-            ++cnt;
+        const int cnt = (int)std::min<size_t>(bj.size() - off, (size_t)SERVE_PLAN_JOBS);
+        size_t sb = 0;
+        int64_t words = 0;
+        batch_layout(bj.data() + off, cnt, &sb, &words);
+        void* sc = nullptr;
+        cudaError_t e = cudaMallocFromPoolAsync(&sc, sb > 0 ? sb : 256, s->pool, st);
+        if (e != cudaSuccess) {
+            status = cuda_fail(e, "serve: batch scratch");
+            break;
         }
-        status = edt_batch(slot.plan, bj.data() + off, (int)cnt, (edt_stream_t)st);
+        bscratch.push_back(sc);
+        status = batch_enqueue(slot.plan, bj.data() + off, cnt, static_cast<char*>(sc), st);
         off += cnt;
     }
+    for (void* sc : bscratch) cudaFreeAsync(sc, st);
     for (size_t k = 0; k < batch.size(); ++k) {
         const Pending& p = batch[k];
         const Dev& d = dev[k];
@@ -218,14 +240,20 @@ void launch_batch(edt_server* s, int si, std::vector<Pending>& batch, size_t byt
         if (d.dist) cudaFreeAsync(d.dist, st);
         if (d.scratch) cudaFreeAsync(d.scratch, st);
     }
-    Completion* c = new Completion{s, si, bytes, {}, status};
+    Completion* c = new Completion{bytes, {}, status};
     for (const Pending& p : batch) c->tickets.push_back(p.ticket);
-    if (cudaLaunchHostFunc(st, on_batch_done, c) != cudaSuccess) {
-        // the stream is broken: complete the tickets from here
+    cudaError_t e = cudaEventRecord(slot.done, st);
+    if (e != cudaSuccess) {
+        // the stream is broken: wait for what was enqueued, fail the tickets
         cudaStreamSynchronize(st);
-        c->status = EDT_ERR_CUDA;
-        on_batch_done(c);
+        c->status = cuda_fail(e, "serve: cudaEventRecord");
+        cudaEventRecord(slot.done, 0);
     }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        slot.pending = c;
+    }
+    s->cv.notify_all();
 }
 
 void scheduler(edt_server* s)
@@ -260,7 +288,13 @@ void scheduler(edt_server* s)
         }
         s->in_use += bytes;
         s->slots[si].busy = true;
-        for (const Pending& p : batch) s->tickets[p.ticket].state = 1;
+        const auto now = Clock::now();
+        for (const Pending& p : batch) {
+            Ticket& t = s->tickets[p.ticket];
+            t.state = 1;
+            t.t_admit = now;
+            t.wait = std::chrono::duration<double>(now - t.t_submit).count();
+        }
         lk.unlock();
         launch_batch(s, si, batch, bytes);
         lk.lock();
@@ -285,23 +319,28 @@ extern "C" edt_status edt_serve_create(edt_server** out, size_t mem_budget_bytes
     edt_server* s = new edt_server();
     cudaGetDevice(&s->device);
     s->sm_count = sms;
-    // each stream's plan takes about 0.26 B/pixel of scratch for plan_pixels
-    s->plan_pixels = (int64_t)std::min<double>((double)mem_budget_bytes / 9.5 / n_streams, 1.5e9);
-    if (s->plan_pixels < 4096) s->plan_pixels = 4096;
+    // the batches' column-pass scratch comes from the pool with the jobs; a
+    // plan keeps its job tables, its counters and a small scratch of its own
+    s->plan_pixels = 4096;
     size_t reserved = 0;
+    s->slots.reserve((size_t)n_streams);
     for (int k = 0; k < n_streams; ++k) {
-        StreamSlot slot;
+        s->slots.emplace_back();
+        StreamSlot& slot = s->slots.back();
         cudaError_t e = cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamCreate"); break; }
+        // the completion thread spins on this event (no interrupt wake-up): it
+        // frees the stream for the next batch as soon as the device is done
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamCreate / cudaEventCreate"); break; }
         st = edt_plan_create(&slot.plan, SERVE_PLAN_JOBS, s->plan_pixels);
-        if (st != EDT_OK) { cudaStreamDestroy(slot.stream); break; }
-        reserved += (size_t)(0.26 * (double)s->plan_pixels) + (size_t)SERVE_PLAN_JOBS * (16 * BATCH_MAX_W + 1024);
-        s->slots.push_back(slot);
+        if (st != EDT_OK) break;
+        reserved += (size_t)SERVE_PLAN_JOBS * (16 * BATCH_MAX_W + 1024 + sizeof(BatchJob)) + ((size_t)1 << 20);
     }
     if (st != EDT_OK || reserved >= mem_budget_bytes) {
         for (auto& slot : s->slots) {
-            edt_plan_destroy(slot.plan);
-            cudaStreamDestroy(slot.stream);
+            if (slot.plan) edt_plan_destroy(slot.plan);
+            if (slot.done) cudaEventDestroy(slot.done);
+            if (slot.stream) cudaStreamDestroy(slot.stream);
         }
         delete s;
         if (st == EDT_OK) return fail(EDT_ERR_BUDGET, "budget of %zu bytes is below the plans' %zu", mem_budget_bytes, reserved);
@@ -333,12 +372,14 @@ extern "C" edt_status edt_serve_create(edt_server** out, size_t mem_budget_bytes
             if (s->pool) cudaMemPoolDestroy(s->pool);
             for (auto& slot : s->slots) {
                 edt_plan_destroy(slot.plan);
+                cudaEventDestroy(slot.done);
                 cudaStreamDestroy(slot.stream);
             }
             delete s;
             return err;
         }
     }
+    for (int k = 0; k < (int)s->slots.size(); ++k) s->slots[k].completer = std::thread(completer, s, k);
     s->sched = std::thread(scheduler, s);
     *out = s;
     clear_error();
@@ -390,6 +431,21 @@ extern "C" edt_status edt_serve_poll(edt_server* s, uint64_t ticket, double* lat
     return EDT_OK;
 }
 
+extern "C" edt_status edt_serve_poll_detail(edt_server* s, uint64_t ticket, double* latency_s, double* wait_s)
+{
+    if (!s) return fail(EDT_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return fail(EDT_ERR_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    if (it->second.state != 2) return EDT_ERR_NOT_READY;
+    const edt_status st = it->second.status;
+    if (latency_s) *latency_s = it->second.latency;
+    if (wait_s) *wait_s = it->second.wait;
+    s->tickets.erase(it);
+    if (st != EDT_OK) return fail(st, "served job failed");
+    return EDT_OK;
+}
+
 extern "C" edt_status edt_serve_destroy(edt_server* s)
 {
     if (!s) return EDT_OK;
@@ -401,9 +457,16 @@ extern "C" edt_status edt_serve_destroy(edt_server* s)
     }
     s->cv.notify_all();
     if (s->sched.joinable()) s->sched.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->cv.notify_all();
+    }
+    for (auto& slot : s->slots)
+        if (slot.completer.joinable()) slot.completer.join();
     for (auto& slot : s->slots) {
         cudaStreamSynchronize(slot.stream);
         edt_plan_destroy(slot.plan);
+        cudaEventDestroy(slot.done);
         cudaStreamDestroy(slot.stream);
     }
     if (s->pool) cudaMemPoolDestroy(s->pool);

@@ -6,12 +6,17 @@
 // for the 3-D y pass, 32 for the x pass, fewer when shared memory does not
 // fit) were measured on the benchmark shapes; edt_autotune times the
 // candidates on the caller's own mask and keeps the fastest for its shape
-// class.  A choice never changes a result: every segmentation gives the same
-// D and F, bit for bit.
+// class.  edt_autotune_batch does the same for the geometry of the batch
+// kernels (the smallest row segment of narrow 2-D jobs, the positions per warp
+// of the 3-D y and x passes), timing each shape class of the caller's batch
+// on its own.  A choice never changes a result: every segmentation gives the
+// same D and F, bit for bit.
+#include <algorithm>
 #include <array>
 #include <cstdio>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "edt_internal.h"
 
@@ -32,6 +37,7 @@ using Key = std::array<int, 4>;   // ndim, then ceil(log2(side)) per axis
 
 std::mutex g_tune_mu;
 std::map<Key, Tuning> g_tune;
+std::map<Key, BatchTuning> g_btune;    // batch geometry per shape class
 
 int ceil_log2(int v)
 {
@@ -62,6 +68,22 @@ void tuning_store(int ndim, const int* shape, const Tuning& t)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key_of(ndim, shape)] = t;
 }
+
+BatchTuning batch_tuning_lookup(int ndim, const int* shape)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_btune.empty()) return BatchTuning{};
+    auto it = g_btune.find(key_of(ndim, shape));
+    return it == g_btune.end() ? BatchTuning{} : it->second;
+}
+
+void batch_tuning_store(int ndim, const int* shape, const BatchTuning& t)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_btune[key_of(ndim, shape)] = t;
+}
+
+edt_status batch_enqueue(edt_plan* p, const edt_job* jobs, int n, char* scratch, cudaStream_t stream);
 
 }  // namespace edt
 
@@ -146,6 +168,103 @@ extern "C" edt_status edt_autotune(const uint8_t* mask, int ndim, const int* sha
     return st;
 }
 
+extern "C" edt_status edt_autotune_batch(edt_plan* plan, const edt_job* jobs, int n, edt_stream_t stream_)
+{
+    if (!plan || !jobs || n <= 0) return fail(EDT_ERR_INVALID, "plan, jobs and n > 0 are required");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    for (int i = 0; i < n; ++i) {
+        edt_status st = check_shape(jobs[i].ndim, jobs[i].shape, jobs[i].mode);
+        if (st != EDT_OK) return st;
+        const char* why = "";
+        if (!jobs[i].mask || !jobs[i].F) return fail(EDT_ERR_INVALID, "job %d: mask and F must not be NULL", i);
+        if (batch_kind(jobs[i], &why) < 0) return fail(EDT_ERR_TOO_LARGE, "job %d: %s", i, why);
+    }
+    // the jobs of each shape class, timed on their own
+    std::map<Key, std::vector<edt_job>> classes;
+    for (int i = 0; i < n; ++i) classes[key_of(jobs[i].ndim, jobs[i].shape)].push_back(jobs[i]);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    edt_status st = EDT_OK;
+    cudaError_t e;
+    for (auto& x : ev)
+        if (st == EDT_OK && (e = cudaEventCreate(&x)) != cudaSuccess) st = cuda_fail(e, "cudaEventCreate");
+    for (auto& kv : classes) {
+        if (st != EDT_OK) break;
+        std::vector<edt_job>& cj = kv.second;
+        const edt_job& j0 = cj[0];
+        const int kind = batch_kind(j0, nullptr);
+        if (kind == BATCH_2D_WIDE) continue;   // no knob
+        auto time_with = [&](const BatchTuning& t) -> float {
+            batch_tuning_store(j0.ndim, j0.shape, t);
+            float total = 0.f;
+            for (size_t off = 0; off < cj.size(); off += (size_t)256) {
+                const int cnt = (int)std::min<size_t>(256, cj.size() - off);
+                if (batch_enqueue(plan, cj.data() + off, cnt, nullptr, stream) != EDT_OK) return -1.f;
+                cudaEventRecord(ev[0], stream);
+                for (int r = 0; r < 3; ++r)
+                    if (batch_enqueue(plan, cj.data() + off, cnt, nullptr, stream) != EDT_OK) return -1.f;
+                cudaEventRecord(ev[1], stream);
+                if (cudaEventSynchronize(ev[1]) != cudaSuccess) return -1.f;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                total += ms / 3;
+            }
+            return total;
+        };
+        BatchTuning best{};
+        float best_ms = -1.f;
+        auto consider = [&](const BatchTuning& t) {
+            const float ms = time_with(t);
+            if (ms < 0) { st = fail(EDT_ERR_CUDA, "autotune_batch: a candidate failed"); return; }
+            if (best_ms < 0 || ms < best_ms) { best_ms = ms; best = t; }
+        };
+        if (kind == BATCH_2D) {
+            for (int lgmin : {8, 7, 6}) {
+                BatchTuning t;
+                t.rows2d_lgmin = lgmin;
+                consider(t);
+                if (st != EDT_OK) break;
+            }
+        } else {
+            for (int pos : {64, 32, 128}) {      // y pass, x pass at its rule
+                BatchTuning t;
+                t.y_pos = pos;
+                t.x_pos = 32;
+                consider(t);
+                if (st != EDT_OK) break;
+            }
+            const int ybest = best.y_pos;
+            for (int pos : {64, 128}) {
+                if (st != EDT_OK) break;
+                BatchTuning t;
+                t.y_pos = ybest;
+                t.x_pos = pos;
+                consider(t);
+            }
+        }
+        batch_tuning_store(j0.ndim, j0.shape, st == EDT_OK ? best : BatchTuning{});
+    }
+    e = cudaStreamSynchronize(stream);
+    if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    if (st == EDT_OK) clear_error();
+    return st;
+}
+
+extern "C" edt_status edt_batch_tune_get(int ndim, const int* shape, int* values)
+{
+    if (!shape || !values) return fail(EDT_ERR_INVALID, "NULL argument");
+    if (ndim != 2 && ndim != 3) return fail(EDT_ERR_INVALID, "ndim must be 2 or 3, got %d", ndim);
+    for (int a = 0; a < ndim; ++a)
+        if (shape[a] <= 0) return fail(EDT_ERR_INVALID, "shape[%d] = %d must be positive", a, shape[a]);
+    const BatchTuning t = batch_tuning_lookup(ndim, shape);
+    values[0] = t.rows2d_lgmin;
+    values[1] = t.y_pos;
+    values[2] = t.x_pos;
+    clear_error();
+    return EDT_OK;
+}
+
 extern "C" edt_status edt_tune_get(int ndim, const int* shape, int* warps)
 {
     if (!shape || !warps) return fail(EDT_ERR_INVALID, "NULL argument");
@@ -171,6 +290,10 @@ extern "C" edt_status edt_tune_save(const char* path)
         for (const auto& kv : g_tune)
             std::fprintf(f, "%d %d %d %d %d %d %d\n", kv.first[0], kv.first[1], kv.first[2], kv.first[3],
                          kv.second.rows2d_nw, kv.second.ypass_nw, kv.second.xpass_nw);
+        std::fprintf(f, "# batch: b ndim log2-sides(3) rows2d_min_segment_log2 ypass_positions xpass_positions\n");
+        for (const auto& kv : g_btune)
+            std::fprintf(f, "b %d %d %d %d %d %d %d\n", kv.first[0], kv.first[1], kv.first[2], kv.first[3],
+                         kv.second.rows2d_lgmin, kv.second.y_pos, kv.second.x_pos);
     }
     const bool ok = std::fclose(f) == 0;
     if (!ok) return fail(EDT_ERR_INVALID, "cannot write %s", path);
@@ -184,11 +307,29 @@ extern "C" edt_status edt_tune_load(const char* path)
     FILE* f = std::fopen(path, "r");
     if (!f) return fail(EDT_ERR_INVALID, "cannot read %s", path);
     std::map<Key, Tuning> loaded;
+    std::map<Key, BatchTuning> bloaded;
     char line[256];
     edt_status st = EDT_OK;
     while (std::fgets(line, sizeof(line), f)) {
         if (line[0] == '#' || line[0] == '\n') continue;
         Key k;
+        if (line[0] == 'b') {
+            BatchTuning b;
+            if (std::sscanf(line + 1, "%d %d %d %d %d %d %d", &k[0], &k[1], &k[2], &k[3], &b.rows2d_lgmin, &b.y_pos,
+                            &b.x_pos) != 7 ||
+                (k[0] != 2 && k[0] != 3)) {
+                st = fail(EDT_ERR_INVALID, "malformed line in %s: %s", path, line);
+                break;
+            }
+            auto ok_pos = [](int v) { return v == 0 || v == 32 || v == 64 || v == 128; };
+            if (!(b.rows2d_lgmin == 0 || (b.rows2d_lgmin >= 6 && b.rows2d_lgmin <= 8)) || !ok_pos(b.y_pos) ||
+                !ok_pos(b.x_pos)) {
+                st = fail(EDT_ERR_INVALID, "batch geometry out of range in %s: %s", path, line);
+                break;
+            }
+            bloaded[k] = b;
+            continue;
+        }
         Tuning t;
         if (std::sscanf(line, "%d %d %d %d %d %d %d", &k[0], &k[1], &k[2], &k[3], &t.rows2d_nw, &t.ypass_nw,
                         &t.xpass_nw) != 7 ||
@@ -208,6 +349,7 @@ extern "C" edt_status edt_tune_load(const char* path)
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         for (const auto& kv : loaded) g_tune[kv.first] = kv.second;
+        for (const auto& kv : bloaded) g_btune[kv.first] = kv.second;
     }
     clear_error();
     return EDT_OK;

@@ -83,6 +83,7 @@ EXPORTS = ("edt_sq2d", "edt_sq3d", "edt_feature", "edt_feature_pair", "edt_featu
            "edt_plan_destroy", "edt_batch", "edt_serve_create", "edt_serve_submit",
            "edt_serve_poll", "edt_serve_destroy", "edt_trace_enable", "edt_trace_read",
            "edt_autotune", "edt_tune_get", "edt_tune_save", "edt_tune_load",
+           "edt_autotune_batch", "edt_batch_tune_get", "edt_serve_poll_detail",
            "edt_last_error", "edt_version")
 
 
@@ -131,6 +132,18 @@ _lib.edt_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.edt_plan_destroy.restype = ctypes.c_int
 _lib.edt_batch.argtypes = [ctypes.c_void_p, ctypes.POINTER(Job), ctypes.c_int, _vp]
 _lib.edt_batch.restype = ctypes.c_int
+_lib.edt_autotune_batch.argtypes = [ctypes.c_void_p, ctypes.POINTER(Job), ctypes.c_int, _vp]
+_lib.edt_autotune_batch.restype = ctypes.c_int
+_lib.edt_batch_tune_get.argtypes = [ctypes.c_int, _i32p, _i32p]
+_lib.edt_batch_tune_get.restype = ctypes.c_int
+
+
+def batch_tune_get(shape):
+    """Batch geometry of a shape's class: {"rows2d_lgmin": .., "y_pos": ..,
+    "x_pos": ..}; 0 = the built-in rule."""
+    v = (ctypes.c_int * 3)()
+    _check(_lib.edt_batch_tune_get(len(shape), _shape_arr(shape), v))
+    return {"rows2d_lgmin": v[0], "y_pos": v[1], "x_pos": v[2]}
 
 
 # The same layout as Job (edt_job), for filling many jobs at once.
@@ -173,8 +186,9 @@ class PreparedBatch:
 
 
 class Plan:
-    """A batch plan (edt_plan_create): runs up to n_max 2-D jobs of at most
-    max_pixels pixels in total as one CUDA-graph replay."""
+    """A batch plan (edt_plan_create): runs up to n_max 2-D and 3-D jobs as one
+    CUDA-graph replay; max_pixels sizes its scratch up front (it grows when a
+    batch needs more)."""
 
     def __init__(self, n_max: int, max_pixels: int):
         self._p = ctypes.c_void_p()
@@ -197,6 +211,13 @@ class Plan:
             return
         self.run(PreparedBatch(jobs), stream)
 
+    def autotune(self, jobs, stream=None):
+        """Time the batch-geometry candidates per shape class on these jobs
+        (edt_autotune_batch); later batches use the fastest.  Synchronous."""
+        pb = jobs if isinstance(jobs, PreparedBatch) else PreparedBatch(jobs)
+        _check(_lib.edt_autotune_batch(self._p, pb.arr.ctypes.data_as(ctypes.POINTER(Job)), len(pb.arr),
+                                       _stream_handle(stream)))
+
     def close(self):
         if self._p:
             _check(_lib.edt_plan_destroy(self._p))
@@ -210,8 +231,8 @@ class Plan:
 
 
 def batch(masks, mode: int = TO_OBJECT, want_dist: bool = False, plan: Plan = None, stream=None):
-    """Transform a list of 2-D CUDA uint8 masks in one batch; returns a list of
-    (D, F[, dist]) tuples."""
+    """Transform a list of 2-D and 3-D CUDA uint8 masks in one batch; returns a
+    list of (D, F[, dist]) tuples."""
     masks = [_mask_arg(m) for m in masks]
     outs = []
     for m in masks:
@@ -235,6 +256,9 @@ _lib.edt_serve_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Job), ctypes.P
 _lib.edt_serve_submit.restype = ctypes.c_int
 _lib.edt_serve_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
 _lib.edt_serve_poll.restype = ctypes.c_int
+_lib.edt_serve_poll_detail.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+_lib.edt_serve_poll_detail.restype = ctypes.c_int
 _lib.edt_serve_destroy.argtypes = [ctypes.c_void_p]
 _lib.edt_serve_destroy.restype = ctypes.c_int
 
@@ -275,6 +299,17 @@ class Server:
         bufs = self._live.pop(ticket, None)
         _check(st)
         return lat.value, bufs[1:]
+
+    def poll_detail(self, ticket: int):
+        """None while running; else (latency_s, wait_s, (D, F, dist)), wait_s =
+        the time from submission to admission to a stream."""
+        lat, wait = ctypes.c_double(), ctypes.c_double()
+        st = _lib.edt_serve_poll_detail(self._s, ctypes.c_uint64(ticket), ctypes.byref(lat), ctypes.byref(wait))
+        if st == EDT_ERR_NOT_READY:
+            return None
+        bufs = self._live.pop(ticket, None)
+        _check(st)
+        return lat.value, wait.value, bufs[1:]
 
     def close(self):
         if self._s:

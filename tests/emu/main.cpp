@@ -22,6 +22,7 @@ using namespace edt;
 // The autotuner's table lives in a file the emulation does not build: the
 // built-in geometry rules apply here.
 Tuning edt::tuning_lookup(int, const int*) { return Tuning{}; }
+BatchTuning edt::batch_tuning_lookup(int, const int*) { return BatchTuning{}; }
 
 static uint64_t rng_state = 12345;
 static double urand()
@@ -121,68 +122,100 @@ static int run3d(int Dz, int H, int W, double p, int mode)
     return bad;
 }
 
-// A batch through the two persistent kernels, laid out as edt_batch lays it
-// out: jobs sorted widest first, per-job scratch with the batch geometry
-// (32-band groups), unit ranges by prefix sums, one work counter.
+// D exactly and F a source at squared distance D, for a Dz x H x W volume.
+static int check_features3d(const std::vector<uint8_t>& mask, int Dz, int H, int W, int mode, const int32_t* D,
+                            const int32_t* F, const std::vector<int32_t>& Do)
+{
+    int bad = 0;
+    const size_t n = (size_t)Dz * H * W;
+    for (size_t i = 0; i < n && bad < 5; ++i) {
+        if (D[i] != Do[i]) {
+            fprintf(stderr, "3-D D mismatch %dx%dx%d mode %d at %zu: %d vs %d\n", Dz, H, W, mode, i, D[i], Do[i]);
+            ++bad;
+            continue;
+        }
+        if (Do[i] == INT32_MAX) {
+            if (F[i] != -1) { fprintf(stderr, "3-D F not -1 at %zu\n", i); ++bad; }
+            continue;
+        }
+        const int64_t q = F[i];
+        const bool src = q >= 0 && (size_t)q < n && (mode == 0 ? mask[q] != 0 : mask[q] == 0);
+        const int64_t plane = (int64_t)H * W;
+        const int64_t dz = (int64_t)(i / plane) - q / plane, dy = (int64_t)((i % plane) / W) - (q % plane) / W,
+                      dx = (int64_t)(i % W) - q % W;
+        if (!src || dz * dz + dy * dy + dx * dx != Do[i]) {
+            fprintf(stderr, "3-D F invalid %dx%dx%d at %zu\n", Dz, H, W, i);
+            ++bad;
+        }
+    }
+    return bad;
+}
+
+// A batch of mixed jobs (2-D up to 2048 wide, wider 2-D, 3-D) through the
+// persistent kernels, with the table built by the library's batch_fill.
 static int run_batch(int njobs, int blocks)
 {
     struct Job {
         std::vector<uint8_t> mask;
-        int H, W, mode;
+        int ndim, shape[3], mode;
         int32_t *D, *F;
-        std::vector<unsigned char> scratch;
+        size_t n;
     };
     std::vector<Job> js(njobs);
     const double ps[] = {0.0, 0.001, 0.02, 0.3, 1.0};
     for (int k = 0; k < njobs; ++k) {
         Job& j = js[k];
-        j.H = 1 + (int)(urand() * 300);
-        j.W = 1 + (int)(urand() * (k % 3 == 0 ? 2048 : 300));
+        const int kind = k % 4;
+        if (kind == 3) {
+            j.ndim = 3;
+            j.shape[0] = 1 + (int)(urand() * 40);
+            j.shape[1] = 1 + (int)(urand() * 70);
+            j.shape[2] = 1 + (int)(urand() * 90);
+        } else {
+            j.ndim = 2;
+            j.shape[0] = 1 + (int)(urand() * (kind == 2 ? 70 : 300));
+            j.shape[1] = 1 + (int)(kind == 0 ? urand() * 2048 : kind == 2 ? 2049 + urand() * 3000 : urand() * 300);
+            j.shape[2] = 0;
+        }
         j.mode = k & 1;
         const double p = ps[k % 5];
-        j.mask.resize((size_t)j.H * j.W);
+        j.n = (size_t)j.shape[0] * j.shape[1] * (j.ndim == 3 ? j.shape[2] : 1);
+        j.mask.resize(j.n);
         for (auto& m : j.mask) m = urand() < p;
-        j.D = alloc_words((size_t)j.H * j.W);
-        j.F = alloc_words((size_t)j.H * j.W);
+        j.D = alloc_words(j.n);
+        j.F = alloc_words(j.n);
     }
-    std::vector<int> order(njobs);
-    for (int k = 0; k < njobs; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return js[a].W > js[c].W; });
+    std::vector<edt_job> ej(njobs);
+    for (int k = 0; k < njobs; ++k) {
+        Job& j = js[k];
+        ej[k] = edt_job{j.mask.data(), j.ndim, {j.shape[0], j.shape[1], j.shape[2]}, j.mode, j.D, j.F, nullptr};
+        if (batch_kind(ej[k], nullptr) < 0) { fprintf(stderr, "job %d not batchable\n", k); return 1; }
+    }
+    size_t sb = 0;
+    int64_t cw = 0;
+    batch_layout(ej.data(), njobs, &sb, &cw);
+    std::vector<unsigned char> scratch(sb + 256), cnt((size_t)cw * 4 + 256, 0xAB);
     std::vector<unsigned char> table(sizeof(BatchHeader) + (size_t)njobs * sizeof(BatchJob) + 256);
     auto* hdr = reinterpret_cast<BatchHeader*>(((uintptr_t)table.data() + 255) & ~uintptr_t(255));
     auto* tab = reinterpret_cast<BatchJob*>(hdr + 1);
-    int64_t k1 = 0, k2 = 0;
-    for (int t = 0; t < njobs; ++t) {
-        Job& j = js[order[t]];
-        BatchJob& J = tab[t];
-        memset(&J, 0, sizeof(J));
-        J.mask = j.mask.data();
-        J.D = j.D;
-        J.F = j.F;
-        J.dist = nullptr;
-        J.g = col_geom(j.H, j.W, true);
-        J.mode = j.mode;
-        J.vec = (j.W % 16 == 0) && ((reinterpret_cast<uintptr_t>(j.mask.data()) & 15) == 0);
-        j.scratch.assign(col_scratch_bytes(J.g) + 256, 0);
-        J.s = col_scratch_carve((void*)(((uintptr_t)j.scratch.data() + 255) & ~uintptr_t(255)), J.g);
-        batch_row_geometry(j.W, J.lg, J.NW, J.groups);
-        J.k1_first = k1;
-        J.k2_first = k2;
-        k1 += J.g.ntiles * (int64_t)J.g.nG;
-        k2 += (J.g.nb + J.groups - 1) / J.groups;
-    }
-    hdr->njobs = njobs;
-    hdr->pad0 = 0;
-    hdr->k1_total = k1;
-    hdr->k2_total = k2;
-    unsigned work = 0;
+    batch_fill(ej.data(), njobs, (char*)(((uintptr_t)scratch.data() + 255) & ~uintptr_t(255)),
+               (unsigned*)(((uintptr_t)cnt.data() + 255) & ~uintptr_t(255)), hdr, tab);
+    launch_batch_clear(hdr, blocks, nullptr);
     launch_batch_colbits(hdr, tab, blocks, nullptr);
-    launch_batch_rows2d(hdr, tab, &work, blocks, nullptr);
+    launch_batch_rows2d(hdr, tab, blocks, nullptr);
+    launch_batch_wide(hdr, tab, blocks, nullptr);
+    launch_batch_ypass3d(hdr, tab, blocks, nullptr);
+    launch_batch_xpass3d(hdr, tab, blocks, nullptr);
     int bad = 0;
     for (Job& j : js) {
-        std::vector<int32_t> Do((size_t)j.H * j.W), Fo((size_t)j.H * j.W);
-        oracle_edt2d(j.mask.data(), j.H, j.W, j.mode, Do.data(), Fo.data());
-        bad += check_features(j.mask, j.H, j.W, j.mode, j.D, j.F, Do);
+        std::vector<int32_t> Do(j.n), Fo(j.n);
+        if (j.ndim == 2) {
+            oracle_edt2d(j.mask.data(), j.shape[0], j.shape[1], j.mode, Do.data(), Fo.data());
+            bad += check_features(j.mask, j.shape[0], j.shape[1], j.mode, j.D, j.F, Do);
+        } else {
+            oracle_edt3d(j.mask.data(), j.shape[0], j.shape[1], j.shape[2], j.mode, Do.data(), Fo.data());
+            bad += check_features3d(j.mask, j.shape[0], j.shape[1], j.shape[2], j.mode, j.D, j.F, Do);
+        }
         free(j.D);
         free(j.F);
     }

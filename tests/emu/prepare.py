@@ -9,7 +9,8 @@ here = os.path.dirname(os.path.abspath(__file__))
 src = os.path.join(here, "../../paper_2106_03503_gb300/csrc")
 out = sys.argv[1] if len(sys.argv) > 1 else os.path.join(here, "_build", "src")
 os.makedirs(out, exist_ok=True)
-for name in ["edt_engine.cuh", "edt_internal.h", "edt_colpass.cu", "edt_rows2d.cu", "edt_3d.cu", "edt_cityblock.cu", "edt_chamfer.cu"]:
+for name in ["edt_engine.cuh", "edt_internal.h", "edt_colpass.cu", "edt_rows2d.cu", "edt_3d.cu", "edt_cityblock.cu",
+             "edt_chamfer.cu", "edt_batch_table.cu"]:
     s = open(os.path.join(src, name)).read()
     s = s.replace("#include <cuda.h>", '#include "shim.h"').replace("#include <cuda_runtime.h>", '#include "shim.h"')
     s = s.replace('#include "../../include/edt.h"', '#include "edt.h"')

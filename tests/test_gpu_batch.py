@@ -81,20 +81,111 @@ def test_batch_errors():
     import torch
     from paper_2106_03503_gb300 import edt
     plan = edt.Plan(2, 10_000)
-    m3 = torch.zeros((4, 5, 6), dtype=torch.uint8, device="cuda")
-    F3 = torch.empty((4, 5, 6), dtype=torch.int32, device="cuda")
+    # a volume whose rows are wider than the batched x pass holds
+    m3 = torch.zeros((2, 4, 1000), dtype=torch.uint8, device="cuda")
+    F3 = torch.empty((2, 4, 1000), dtype=torch.int32, device="cuda")
     with pytest.raises(edt.EdtError) as e:
         plan.run([(m3, 0, None, F3, None)])
-    assert e.value.status == 1
-    wide = torch.zeros((2, 2049), dtype=torch.uint8, device="cuda")
-    Fw = torch.empty((2, 2049), dtype=torch.int32, device="cuda")
-    with pytest.raises(edt.EdtError) as e:
-        plan.run([(wide, 0, None, Fw, None)])
     assert e.value.status == 2
     m = torch.zeros((10, 10), dtype=torch.uint8, device="cuda")
     F = torch.empty((10, 10), dtype=torch.int32, device="cuda")
     with pytest.raises(edt.EdtError):
-        plan.run([(m, 0, None, F, None)] * 3)
+        plan.run([(m, 0, None, F, None)] * 3)            # more jobs than n_max
+    with pytest.raises(edt.EdtError) as e:
+        plan.run([(m, 5, None, F, None)])                # bad mode
+    assert e.value.status == 1
+    plan.close()
+
+
+def _mixed_specs(rng, n):
+    """2-D jobs up to 2048 wide, wider 2-D jobs and 3-D volumes, mixed."""
+    specs = []
+    for k in range(n):
+        kind = k % 4
+        p = float(rng.choice([0.0, 0.0007, 0.01, 0.2, 0.9, 1.0]))
+        if kind == 3:
+            shape = (int(rng.integers(1, 70)), int(rng.integers(1, 130)), int(rng.integers(1, 300)))
+        elif kind == 2:
+            shape = (int(rng.integers(1, 200)), int(rng.integers(2049, 9000)))
+        else:
+            shape = (int(rng.integers(1, 700)), int(rng.integers(1, 2049)))
+        specs.append((shape, p, int(rng.integers(2)), bool(rng.integers(2)), bool(rng.integers(2))))
+    return specs
+
+
+def _run_mixed(torch, edt, plan, specs, seed):
+    jobs = []
+    for k, (shape, p, mode, want_D, want_dist) in enumerate(specs):
+        m_np = inputs.bernoulli_mask(shape, p, seed * 1000 + k)
+        m = torch.from_numpy(m_np).cuda()
+        D = torch.full(shape, -5, dtype=torch.int32, device="cuda") if want_D else None
+        F = torch.full(shape, -5, dtype=torch.int32, device="cuda")
+        dist = torch.full(shape, -5.0, dtype=torch.float32, device="cuda") if want_dist else None
+        jobs.append((m, mode, D, F, dist))
+    plan.run(jobs)
+    torch.cuda.synchronize()
+    return jobs
+
+
+def test_mixed_2d_3d_wide_batch_matches_oracle():
+    """One replay with narrow 2-D, wide 2-D (beyond 2048 columns) and 3-D jobs
+    of uneven sizes, both modes, optional outputs: every job against the
+    oracle and bit-identical to a plain call."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    rng = np.random.default_rng(3)
+    specs = _mixed_specs(rng, 40)
+    plan = edt.Plan(len(specs), 1 << 20)     # small scratch up front: the plan grows
+    for rep in range(2):
+        jobs = _run_mixed(torch, edt, plan, specs, 40 + rep)
+        refs = [edt.feature(m, mode, want_dist=True) for (m, mode, _, _, _) in jobs]
+        _check(jobs, refs, torch)
+    plan.close()
+
+
+def test_batch_autotune_candidates_give_the_same_bits(tmp_path):
+    """edt_autotune_batch picks a geometry per shape class; every candidate
+    (forced through a tuning file) gives the same D, F bits as a plain call."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    rng = np.random.default_rng(5)
+    specs = [((int(rng.integers(100, 600)), int(rng.integers(100, 1500))), 0.01, 0, True, False)
+             for _ in range(6)]
+    specs += [((int(rng.integers(20, 60)), int(rng.integers(40, 200)), int(rng.integers(40, 260))), 0.0, 0, True,
+               False) for _ in range(4)]
+    plan = edt.Plan(len(specs), 1 << 22)
+    jobs = _run_mixed(torch, edt, plan, specs, 60)
+    for k, (m, mode, D, F, dist) in enumerate(jobs):   # smoothed-noise volumes for the 3-D jobs
+        if m.dim() == 3:
+            jobs[k] = (torch.from_numpy(inputs.smoothed_noise_volume(tuple(m.shape), 3.0, 70 + k)).cuda(), mode, D, F,
+                       dist)
+    refs = [edt.feature(m, mode) for (m, mode, _, _, _) in jobs]
+    plan.autotune(jobs)
+    torch.cuda.synchronize()
+    for (m, mode, D, F, _), (Dr, Fr) in zip(jobs, refs):
+        assert torch.equal(D, Dr) and torch.equal(F, Fr)
+    for lgmin, pos in ((6, 32), (7, 128), (8, 64)):
+        path = tmp_path / f"t{lgmin}.txt"
+        lines = []
+        for (m, _, _, _, _) in jobs:
+            cls = [int(np.ceil(np.log2(v))) if v > 1 else 0 for v in m.shape] + [0] * (3 - m.dim())
+            lines.append(f"b {m.dim()} {cls[0]} {cls[1]} {cls[2]} {lgmin if m.dim() == 2 else 0} "
+                         f"{pos if m.dim() == 3 else 0} {pos if m.dim() == 3 else 0}")
+        path.write_text("\n".join(lines) + "\n")
+        edt.tune_load(str(path))
+        for (m, _, _, _, _) in jobs:
+            got = edt.batch_tune_get(tuple(m.shape))
+            if m.dim() == 2:
+                assert got["rows2d_lgmin"] == lgmin
+            else:
+                assert got["y_pos"] == pos and got["x_pos"] == pos
+        for (m, mode, D, F, dist) in jobs:
+            D.fill_(-9)
+            F.fill_(-9)
+        plan.run(jobs)
+        torch.cuda.synchronize()
+        for (m, mode, D, F, _), (Dr, Fr) in zip(jobs, refs):
+            assert torch.equal(D, Dr) and torch.equal(F, Fr), (lgmin, pos, tuple(m.shape))
     plan.close()
 
 

@@ -1,5 +1,7 @@
 """The CUDA kernels of libedt (column pass, 2-D row pass alone and fused for
-both transforms, 3-D y and x passes, city-block row pass, chamfer 4-3 passes) compiled as C++ and run on the CPU by a
+both transforms, 3-D y and x passes, city-block row pass, chamfer 4-3 passes,
+the persistent batch kernels on mixed 2-D / wide 2-D / 3-D batches laid out by
+the library's own table builder) compiled as C++ and run on the CPU by a
 host emulation (tests/emu): one fiber per CUDA thread, barriers and warp
 collectives emulated, dynamic shared memory allocated at exactly the
 launch's size under AddressSanitizer.  The results must equal the oracle's
@@ -40,7 +42,8 @@ def _build():
            "-include", os.path.join(EMU, "shim.h")] + san + [
         "-x", "c++", os.path.join(src, "edt_colpass.cu"), "-x", "c++", os.path.join(src, "edt_rows2d.cu"),
         "-x", "c++", os.path.join(src, "edt_3d.cu"), "-x", "c++", os.path.join(src, "edt_cityblock.cu"),
-        "-x", "c++", os.path.join(src, "edt_chamfer.cu"), "-x", "none", os.path.join(EMU, "runtime.cpp"),
+        "-x", "c++", os.path.join(src, "edt_chamfer.cu"), "-x", "c++", os.path.join(src, "edt_batch_table.cu"),
+        "-x", "none", os.path.join(EMU, "runtime.cpp"),
         os.path.join(EMU, "main.cpp"), oracle_o, nedt_o, "-o", exe, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -482,7 +482,8 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
     server's per-ticket record splits it into the wait for admission to a
     stream and the time on the stream.  The same job stream then runs through
     the plain path, one synchronous edt_feature_host call per job, back to
-    back: `served_over_plain` = served throughput at load 1.0 / plain."""
+    back: `served_over_plain` = the highest served throughput of the sweep
+    (load 1.0: arrivals at capacity) / plain."""
     import numpy as np
     from concurrent.futures import ThreadPoolExecutor
     from paper_2106_03503_gb300 import inputs
@@ -575,13 +576,18 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
         edt.feature_host(m, 0, D=D, F=F)
     plain_s = time.perf_counter() - t0
     plain_gpx = sum(pool[int(k)].numel() for k in stream) / plain_s / 1e9
-    main = runs[-1]
+    # the top-level latencies are those of the highest load below capacity;
+    # at load 1.0 arrivals match capacity and the queue grows without bound,
+    # so that run gives the sustained throughput
+    main = max((r for r in runs if r["load"] < 1.0), key=lambda r: r["load"], default=runs[-1])
+    sat = max(runs, key=lambda r: r["throughput_gpx_s"])
     return {"workload": "Poisson stream, 80% 2D side 128-4096 Bernoulli p log-uniform 0.001-0.1, "
                         "20% 3D side 64-256 smoothed noise; 40 GB budget, 3 streams, host buffers",
             "capacity_gpx_s": cap_px / 1e9, "warmup_jobs": warm,
             "load": main["load"], "jobs": main["jobs"], "arrival_rate_jobs_s": main["arrival_rate_jobs_s"],
             "throughput_gpx_s": main["throughput_gpx_s"], "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
-            "plain_gpx_s": plain_gpx, "served_over_plain": main["throughput_gpx_s"] / plain_gpx,
+            "sustained_gpx_s": sat["throughput_gpx_s"],
+            "plain_gpx_s": plain_gpx, "served_over_plain": sat["throughput_gpx_s"] / plain_gpx,
             "plain": "the same job stream, one synchronous edt_feature_host call per job",
             "sweep": runs,
             "note": f"{pool_size} distinct masks of the recipe (pinned, drawn untimed), each job one of them; "

@@ -75,9 +75,10 @@ struct OutY {
     }
 };
 
+// y tile: nearest z of [H][32] (int16), per-warp maxima (32 ints), engine
 __host__ __device__ static inline size_t ypass_smem(int H, int lg, int NW)
 {
-    return (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + band_smem_bytes(NW, (1 << lg) >> 5);
+    return (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + 128 + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
 size_t batch_ypass_group_bytes(int H, int lg, int NW) { return ypass_smem(H, lg, NW); }
@@ -90,13 +91,16 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, ui
                            int z, int x0, unsigned char* base, int tid, int nthr, int warp, Sync sync)
 {
     short* gz = reinterpret_cast<short*>(base);
-    const BandSmem sm = carve_band_smem(base + (((size_t)H * 32 * 2 + 15) & ~size_t(15)), NW,
+    int* wmax = reinterpret_cast<int*>(base + (((size_t)H * 32 * 2 + 15) & ~size_t(15)));
+    const BandSmem sm = carve_band_smem(base + (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + 128, NW,
                                         (1 << lg) >> 5);
     const int lane = tid & 31;
     const int64_t plane = (int64_t)H * W;
     const int zb = z >> 5, zr = z & 31, zG = zb >> s.gs;
 
-    // nearest source along z of every (y, x) of the tile
+    // nearest source along z of every (y, x) of the tile, and the largest
+    // z distance among them (columns past the volume's edge count as 0)
+    int dmax = 0;
     for (int e = tid; e < H * 32; e += nthr) {
         const int y = e >> 5, xl = e & 31, x = x0 + xl;
         int g = -1;
@@ -111,14 +115,21 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, ui
                 if (dn == (uint32_t)NONE16) dn = gab >> 16;
             }
             g = nearest_in_column(w, zb * 32, zr, (int)up, (int)dn);
+            dmax = max(dmax, g < 0 ? 32767 : abs(z - g));
         }
         gz[e] = (short)g;
     }
+    dmax = (int)__reduce_max_sync(FULL, (unsigned)dmax);
+    if (lane == 0) wmax[warp] = dmax;
     sync();
+    for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
 
     const LineY line{gz, lane, z};
     const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
-    band_envelope(line, out, sm, H, lg, NW, nullptr, warp, sync);
+    if (dmax <= DIRECT_MAX_DIST)
+        band_direct(line, out, H, warp, NW);      // near answers: no hull, no barrier
+    else
+        band_envelope(line, out, sm, H, lg, NW, nullptr, warp, sync);
 }
 
 // One block: one z, 32 consecutive x (one line per lane), warps = y segments.
@@ -177,9 +188,10 @@ struct LineX {
 
 __host__ __device__ static inline int xpass_pitch(int W) { return W | 1; }
 
+// x unit: records of [32][pitch], per-warp maxima (32 ints), engine
 __host__ __device__ static inline size_t xpass_smem(int W, int lg, int NW)
 {
-    return (((size_t)32 * xpass_pitch(W) * 4 + 15) & ~size_t(15)) +
+    return (((size_t)32 * xpass_pitch(W) * 4 + 15) & ~size_t(15)) + 128 +
            band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
@@ -193,17 +205,31 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
 {
     const int pitch = W | 1;
     uint32_t* rec = reinterpret_cast<uint32_t*>(base);   // [32][pitch]
-    const BandSmem sm = carve_band_smem(base + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)), NW,
+    int* wmax = reinterpret_cast<int*>(base + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)));
+    const BandSmem sm = carve_band_smem(base + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)) + 128, NW,
                                         (1 << lg) >> 5);
     const int lane = tid & 31;
     const int64_t nrows = (int64_t)Dz * H;
 
+    // the rows' (z', y') records, and the largest (z, y) distance among them
+    // (rows past the volume's end count as 0)
+    int dmax = 0;
     for (int e = tid; e < 32 * W; e += nthr) {
         const int rl = e / W, k = e - rl * W;
         const int64_t row = row0 + rl;
-        rec[rl * pitch + k] = (row < nrows) ? P[row * W + k] : PNONE;
+        uint32_t p = PNONE;
+        if (row < nrows) {
+            p = P[row * W + k];
+            const int zz = (int)(row / H), yy = (int)(row % H);
+            const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
+            dmax = max(dmax, p == PNONE ? 32767 : max(abs(dz), abs(dy)));
+        }
+        rec[rl * pitch + k] = p;
     }
+    dmax = (int)__reduce_max_sync(FULL, (unsigned)dmax);
+    if (lane == 0) wmax[warp] = dmax;
     sync();
+    for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
 
     const int64_t row = row0 + lane;
     LineX line;
@@ -216,7 +242,12 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
     line.self = ((uint32_t)line.z << 16) | (uint32_t)line.y;
     const int vec = row_vec_width(W, D, F, dist);
     const RowOut out{D, F, dist, row * W, row < nrows, vec};
-    band_envelope(line, out, sm, W, lg, NW, nullptr, warp, sync);
+    // a record at (z, y) distance at most 64 per axis is at most sqrt(2) * 64
+    // away: the search from it ends within that radius
+    if (dmax <= DIRECT_MAX_DIST)
+        band_direct(line, out, W, warp, NW);
+    else
+        band_envelope(line, out, sm, W, lg, NW, nullptr, warp, sync);
 }
 
 // One block: 32 consecutive rows (z, y) of the volume (one per lane), warps =

@@ -601,6 +601,59 @@ __device__ void band_fill(const Line& line, const Out& out, const BandSmem& sm, 
     }
 }
 
+// Direct minimum for lines whose answers are near: position j takes the
+// minimum over k of f(k) + (j - k)^2 (Eq. (5)), searched outward from j,
+// r = 0, 1, 2, ..., until r^2 is no smaller than the best value found --
+// every k farther away costs at least r^2, so the result is exact.  At a tie
+// the rightmost k is kept (a candidate left of the current best must be
+// strictly smaller, one right of it may tie), the same choice as the hull
+// walk of band_fill.  Each warp takes every NW-th chunk of OC positions of the
+// 32 lines; no barrier, no shared state.  Line and Out as for band_envelope.
+template <class Line, class Out>
+__device__ void band_direct(const Line& line, const Out& out, int n, int warp, int NW)
+{
+    const int nq = (n + OC - 1) / OC;
+    for (int q = warp; q < nq; q += NW) {
+        const int j0 = q * OC;
+        int v[OC], ft[OC];
+#pragma unroll
+        for (int t = 0; t < OC; ++t) {
+            const int j = j0 + t;
+            v[t] = INT32_MAX;
+            ft[t] = -1;
+            if (j >= n) continue;
+            int f, best = INT32_MAX, bk = -1;
+            if (line.eval(j, f)) {
+                best = f;
+                bk = j;
+            }
+            for (int r = 1; r < n && r * r < best; ++r) {
+                if (j - r >= 0 && line.eval(j - r, f) && f + r * r < best) {
+                    best = f + r * r;
+                    bk = j - r;
+                }
+                if (j + r < n && line.eval(j + r, f) && f + r * r <= best) {
+                    best = f + r * r;
+                    bk = j + r;
+                }
+            }
+            if (bk >= 0) {
+                int g;
+                line.eval2(bk, f, g);
+                v[t] = best;
+                ft[t] = g;
+            }
+        }
+        out.store(j0, min(OC, n - j0), v, ft);
+    }
+    out.finish();
+}
+
+// Largest own value (as a distance, saturated at 2^15) at which an engine
+// takes the direct search instead of the hull: the search from a position
+// ends within sqrt of its answer, which is at most its own value.
+constexpr int DIRECT_MAX_DIST = 64;
+
 // The whole per-block computation, called by every thread of the block
 // (blockDim.x = 32 * NW, or the NW warps of one group).  Line (per lane) must
 // provide

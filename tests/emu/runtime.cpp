@@ -126,6 +126,16 @@ unsigned __reduce_and_sync(unsigned, unsigned v)
     warp_wait(__builtin_return_address(0));
     return r;
 }
+unsigned __reduce_max_sync(unsigned, unsigned v)
+{
+    const int t = g_f[g_cur].tid;
+    g_slot[t >> 5][t & 31] = v;
+    warp_wait(__builtin_return_address(0));
+    unsigned r = 0u;
+    for (int l = 0; l < 32; ++l) r = g_slot[t >> 5][l] > r ? g_slot[t >> 5][l] : r;
+    warp_wait(__builtin_return_address(0));
+    return r;
+}
 unsigned char* emu_smem() { return g_smem; }
 size_t emu_smem_bytes() { return g_smem_bytes; }
 

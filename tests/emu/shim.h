@@ -78,6 +78,7 @@ int __shfl_down_sync(unsigned mask, int v, unsigned d);
 unsigned __shfl_xor_sync(unsigned mask, unsigned v, int lanemask);
 unsigned __ballot_sync(unsigned mask, int pred);
 unsigned __reduce_and_sync(unsigned mask, unsigned v);
+unsigned __reduce_max_sync(unsigned mask, unsigned v);
 int __any_sync(unsigned mask, int pred);
 unsigned char* emu_smem();
 size_t emu_smem_bytes();

@@ -23,36 +23,42 @@ constexpr uint32_t PNONE = 0xFFFFFFFFu;
 
 // --- y pass ----------------------------------------------------------------
 
+// y tile data: for each (y, x), d = nearest source z along z minus z (int16,
+// YNONE when the column has no source), [YPAD + H + YPAD][32], the pads
+// holding YNONE so that a search may step past either end.
+constexpr short YNONE = 32767;
+constexpr int YPAD = DIRECT_MAX_DIST;
+
 struct LineY {
-    const short* gz;         // [H][32]: nearest source z of (y', x0 + lane), -1 none
+    const short* gz;         // row y' of this tile at gz[y' * 32] (pads around)
     int lane;
     int z;
     __device__ __forceinline__ bool eval(int k, int& f) const
     {
-        const int g = gz[k * 32 + lane];
-        if (g < 0) return false;
-        f = (z - g) * (z - g);
+        const int d = gz[k * 32 + lane];
+        if (d == YNONE) return false;
+        f = d * d;
         return true;
     }
     __device__ __forceinline__ int c(int k) const
     {
-        const int g = gz[k * 32 + lane];
-        return (z - g) * (z - g) + k * k;
+        const int d = gz[k * 32 + lane];
+        return d * d + k * k;
     }
     __device__ __forceinline__ bool eval2(int k, int& f, int& feat) const
     {
-        const int g = gz[k * 32 + lane];
-        if (g < 0) return false;
-        f = (z - g) * (z - g);
-        feat = (int)(((uint32_t)g << 16) | (uint32_t)k);
+        const int d = gz[k * 32 + lane];
+        if (d == YNONE) return false;
+        f = d * d;
+        feat = (int)(((uint32_t)(z + d) << 16) | (uint32_t)k);
         return true;
     }
-    __device__ __forceinline__ bool is_zero(int k) const { return gz[k * 32 + lane] == z; }
+    __device__ __forceinline__ bool is_zero(int k) const { return gz[k * 32 + lane] == 0; }
     __device__ __forceinline__ bool chunk_has_source(int j0) const
     {
         bool any = false;
 #pragma unroll
-        for (int t = 0; t < OC; ++t) any |= gz[(j0 + t) * 32 + lane] == z;
+        for (int t = 0; t < OC; ++t) any |= gz[(j0 + t) * 32 + lane] == 0;
         return any;
     }
     __device__ __forceinline__ int self_feature(int k) const
@@ -75,10 +81,15 @@ struct OutY {
     }
 };
 
-// y tile: nearest z of [H][32] (int16), per-warp maxima (32 ints), engine
+// y tile: z offsets of [YPAD + H + YPAD][32] (int16), per-warp maxima (32
+// ints), engine
+__host__ __device__ static inline size_t ytile_bytes(int H)
+{
+    return ((size_t)(H + 2 * YPAD) * 32 * 2 + 15) & ~size_t(15);
+}
 __host__ __device__ static inline size_t ypass_smem(int H, int lg, int NW)
 {
-    return (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + 128 + band_smem_bytes(NW, (1 << lg) >> 5);
+    return ytile_bytes(H) + 128 + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
 size_t batch_ypass_group_bytes(int H, int lg, int NW) { return ypass_smem(H, lg, NW); }
@@ -90,21 +101,21 @@ template <class Sync>
 __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, uint32_t* __restrict__ P,
                            int z, int x0, unsigned char* base, int tid, int nthr, int warp, Sync sync)
 {
-    short* gz = reinterpret_cast<short*>(base);
-    int* wmax = reinterpret_cast<int*>(base + (((size_t)H * 32 * 2 + 15) & ~size_t(15)));
-    const BandSmem sm = carve_band_smem(base + (((size_t)H * 32 * 2 + 15) & ~size_t(15)) + 128, NW,
-                                        (1 << lg) >> 5);
+    short* gz = reinterpret_cast<short*>(base) + YPAD * 32;     // row 0 of the tile
+    int* wmax = reinterpret_cast<int*>(base + ytile_bytes(H));
+    const BandSmem sm = carve_band_smem(base + ytile_bytes(H) + 128, NW, (1 << lg) >> 5);
     const int lane = tid & 31;
     const int64_t plane = (int64_t)H * W;
     const int zb = z >> 5, zr = z & 31, zG = zb >> s.gs;
 
-    // nearest source along z of every (y, x) of the tile, and the largest
-    // z distance among them (columns past the volume's edge count as 0)
+    // z offset of the nearest source along z of every (y, x) of the tile, and
+    // the largest distance among them (columns past the volume's edge count
+    // as 0); the pads hold YNONE
     int dmax = 0;
-    for (int e = tid; e < H * 32; e += nthr) {
-        const int y = e >> 5, xl = e & 31, x = x0 + xl;
-        int g = -1;
-        if (x < W) {
+    for (int e = tid; e < (H + 2 * YPAD) * 32; e += nthr) {
+        const int y = (e >> 5) - YPAD, xl = e & 31, x = x0 + xl;
+        int d = YNONE;
+        if (y >= 0 && y < H && x < W) {
             const int64_t p = (int64_t)y * W + x;
             const uint32_t w = s.C[(int64_t)zb * plane + p];
             const uint32_t u = s.U[(int64_t)zb * plane + p];
@@ -114,22 +125,52 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, ui
                 if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
                 if (dn == (uint32_t)NONE16) dn = gab >> 16;
             }
-            g = nearest_in_column(w, zb * 32, zr, (int)up, (int)dn);
-            dmax = max(dmax, g < 0 ? 32767 : abs(z - g));
+            const int g = nearest_in_column(w, zb * 32, zr, (int)up, (int)dn);
+            d = g < 0 ? YNONE : g - z;
+            dmax = max(dmax, abs(d));
         }
-        gz[e] = (short)g;
+        gz[e - YPAD * 32] = (short)d;
     }
     dmax = (int)__reduce_max_sync(FULL, (unsigned)dmax);
     if (lane == 0) wmax[warp] = dmax;
     sync();
     for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
 
-    const LineY line{gz, lane, z};
     const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
-    if (dmax <= DIRECT_MAX_DIST)
-        band_direct(line, out, H, warp, NW);      // near answers: no hull, no barrier
-    else
+    if (dmax <= DIRECT_MAX_DIST) {
+        // near answers: each position searches outward along y (Eq. (5)
+        // minimised exactly, rightmost y' at a tie, as the hull walk); every
+        // own offset is at most DIRECT_MAX_DIST = YPAD, so the search never
+        // leaves the padded tile and needs no bounds or validity test (a pad
+        // or a column without source costs 32767^2, more than any answer)
+        const int nq = (H + OC - 1) / OC;
+        for (int q = warp; q < nq; q += NW) {
+            const int j0 = q * OC;
+            int v[OC], ft[OC];
+#pragma unroll
+            for (int t = 0; t < OC; ++t) {
+                const int j = j0 + t;
+                v[t] = INT32_MAX;
+                ft[t] = -1;
+                if (j >= H || x0 + lane >= W) continue;   // not a voxel of the tile
+                const short* col = gz + lane;
+                const int d0 = col[j * 32];
+                int best = d0 * d0, bk = j;
+                for (int r = 1, r2 = 1; r2 < best; ++r, r2 += 2 * r - 1) {
+                    const int dl = col[(j - r) * 32], dr = col[(j + r) * 32];
+                    const int cl = dl * dl + r2, cr = dr * dr + r2;
+                    if (cl < best) { best = cl; bk = j - r; }
+                    if (cr <= best) { best = cr; bk = j + r; }
+                }
+                v[t] = best;
+                ft[t] = (int)(((uint32_t)(z + col[bk * 32]) << 16) | (uint32_t)bk);
+            }
+            out.store(j0, min(OC, H - j0), v, ft);
+        }
+    } else {
+        const LineY line{gz, lane, z};
         band_envelope(line, out, sm, H, lg, NW, nullptr, warp, sync);
+    }
 }
 
 // One block: one z, 32 consecutive x (one line per lane), warps = y segments.
@@ -212,24 +253,89 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
     const int64_t nrows = (int64_t)Dz * H;
 
     // the rows' (z', y') records, and the largest (z, y) distance among them
-    // (rows past the volume's end count as 0)
+    // (rows past the volume's end count as 0); (z, y) of the unit's first row
+    // once, then stepped row by row, so the loads need no divisions
     int dmax = 0;
-    for (int e = tid; e < 32 * W; e += nthr) {
-        const int rl = e / W, k = e - rl * W;
+    int zz = (int)(row0 / H), yy = (int)(row0 % H);
+    for (int rl = 0; rl < 32; ++rl) {
         const int64_t row = row0 + rl;
-        uint32_t p = PNONE;
-        if (row < nrows) {
-            p = P[row * W + k];
-            const int zz = (int)(row / H), yy = (int)(row % H);
-            const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
-            dmax = max(dmax, p == PNONE ? 32767 : max(abs(dz), abs(dy)));
+        const bool live = row < nrows;
+        const uint32_t* src = P + row * W;
+        uint32_t* dst = rec + rl * pitch;
+        for (int k = tid; k < W; k += nthr) {
+            uint32_t p = PNONE;
+            if (live) {
+                p = src[k];
+                const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
+                dmax = max(dmax, p == PNONE ? 32767 : max(abs(dz), abs(dy)));
+            }
+            dst[k] = p;
         }
-        rec[rl * pitch + k] = p;
+        if (++yy == H) {
+            yy = 0;
+            ++zz;
+        }
     }
     dmax = (int)__reduce_max_sync(FULL, (unsigned)dmax);
     if (lane == 0) wmax[warp] = dmax;
     sync();
     for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
+
+    if (dmax <= DIRECT_MAX_DIST) {
+        // near answers: each warp takes whole rows, its lanes 32 consecutive
+        // x, and searches outward along the row (Eq. (5) minimised exactly,
+        // rightmost x' at a tie, as the hull walk); every candidate at most
+        // about 91 positions away, so the search stays short, neighbouring
+        // lanes search about as far, and D, F, dist go out as 128-byte lines
+        for (int rl = warp; rl < 32; rl += NW) {
+            const int64_t row = row0 + rl;
+            if (row >= nrows) break;
+            const int zz = (int)(row / H), yy = (int)(row % H);
+            const uint32_t* rr = rec + rl * pitch;
+            for (int c0 = 0; c0 < W; c0 += 32) {
+                const int j = c0 + lane;
+                if (j >= W) continue;
+                int best = INT32_MAX, bk = -1;
+                auto cost = [&](int k) -> int {   // (z, y) squared distance of column k's record
+                    const uint32_t p = rr[k];
+                    if (p == PNONE) return INT32_MAX;
+                    const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
+                    return dz * dz + dy * dy;
+                };
+                const int own = cost(j);
+                if (own != INT32_MAX) {
+                    best = own;
+                    bk = j;
+                }
+                for (int r = 1; r < W && r * r < best; ++r) {
+                    if (j - r >= 0) {
+                        const int c = cost(j - r);
+                        if (c != INT32_MAX && c + r * r < best) {
+                            best = c + r * r;
+                            bk = j - r;
+                        }
+                    }
+                    if (j + r < W) {
+                        const int c = cost(j + r);
+                        if (c != INT32_MAX && c + r * r <= best) {
+                            best = c + r * r;
+                            bk = j + r;
+                        }
+                    }
+                }
+                const int64_t q = row * W + j;
+                int f = -1;
+                if (bk >= 0) {
+                    const uint32_t p = rr[bk];
+                    f = (((int)(p >> 16) * H) + (int)(p & 0xFFFFu)) * W + bk;
+                }
+                if (D) D[q] = best;
+                if (F) F[q] = f;
+                if (dist) dist[q] = sqrt_rn_int(best);
+            }
+        }
+        return;
+    }
 
     const int64_t row = row0 + lane;
     LineX line;
@@ -242,12 +348,7 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
     line.self = ((uint32_t)line.z << 16) | (uint32_t)line.y;
     const int vec = row_vec_width(W, D, F, dist);
     const RowOut out{D, F, dist, row * W, row < nrows, vec};
-    // a record at (z, y) distance at most 64 per axis is at most sqrt(2) * 64
-    // away: the search from it ends within that radius
-    if (dmax <= DIRECT_MAX_DIST)
-        band_direct(line, out, W, warp, NW);
-    else
-        band_envelope(line, out, sm, W, lg, NW, nullptr, warp, sync);
+    band_envelope(line, out, sm, W, lg, NW, nullptr, warp, sync);
 }
 
 // One block: 32 consecutive rows (z, y) of the volume (one per lane), warps =

@@ -87,9 +87,21 @@ __host__ __device__ inline size_t band2d_col_bytes(int W)
 {
     return (((size_t)8 * W + (size_t)(W + 31) / 32 + 15) & ~size_t(15));
 }
+// Direct row pass (rows2d_direct): rows up to DIRECT_ROW_W wide, one row's
+// vertical offsets per warp in shared memory, searches give up after
+// DIRECT_ROW_CAP columns.
+constexpr int DIRECT_ROW_W = 1024;
+constexpr int DIRECT_ROW_CAP = 64;
+constexpr short OFF_NONE = -32768;
+
+__host__ __device__ inline size_t direct_row_bytes(int W, int NW)
+{
+    return W <= DIRECT_ROW_W ? (((size_t)NW * W * 2 + 15) & ~size_t(15)) : 0;
+}
+
 static size_t band2d_smem(int W, int lg, int NW)
 {
-    return band2d_col_bytes(W) + band_smem_bytes(NW, (1 << lg) >> 5);
+    return band2d_col_bytes(W) + band_smem_bytes(NW, (1 << lg) >> 5) + direct_row_bytes(W, NW);
 }
 
 // Stage the band's column data: source word, encoded nearest source rows
@@ -124,6 +136,90 @@ __device__ __forceinline__ void stage_band(const ColScratch& s, int b, int H, in
         const uint32_t all = __reduce_and_sync(FULL, w);
         if ((j & 31) == 0) sfull[j >> 5] = (all == FULL) ? 1 : 0;
     }
+}
+
+// Direct row pass of band b (32 rows), for narrow rows: every pixel takes the
+// minimum of Eq. (5) over the columns k of its row, D_v(k) + (j - k)^2, by an
+// outward search from j that stops once r^2 reaches the best value found (the
+// same exact search as band_direct), keeping the rightmost k at a tie, the
+// hull walk's choice.  Here the lanes take 32 consecutive columns of one row:
+// each warp first writes its row's vertical offsets (nearest source row minus
+// the row, int16) into `rowbuf` from the staged column words, then searches
+// and writes whole 128-byte lines of D, F and dist.  A search that reaches
+// DIRECT_ROW_CAP columns with candidates left gives up for the whole band
+// (abort flag): the caller then runs the hull engine, which rewrites every
+// pixel with the same value.  Called by the nthr threads of one engine, which
+// must have cleared *abort before their last barrier; returns true when the
+// band is done (the same answer in every thread).
+template <class Sync>
+__device__ bool rows2d_direct(const uint32_t* sbits, const uint32_t* supdn, int b, int H, int W, int32_t* D,
+                              int32_t* F, float* dist, short* rowbuf, volatile int* abort, int lane, int warp,
+                              int NW, Sync sync)
+{
+    const int base = b * 32, rows = min(32, H - base);
+    for (int r = warp; r < rows; r += NW) {
+        if (*abort) break;
+        const int i = base + r;
+        const uint32_t mle = FULL >> (31 - r), mge = FULL << r;
+        for (int k = lane; k < W; k += 32) {
+            const uint32_t w = sbits[k], ud = supdn[k];
+            const uint32_t a = w & mle, bb = w & mge;
+            const int up = a ? base + 31 - __clz(a) : (int)(short)(ud & 0xFFFFu);
+            const int dn = bb ? base + __ffs(bb) - 1 : (int)(ud >> 16);
+            const int du = i - up, dd = dn - i;
+            rowbuf[k] = min(du, dd) >= 32768 ? OFF_NONE : (short)(du <= dd ? up - i : dn - i);
+        }
+        __syncwarp();
+        bool gave_up = false;
+        for (int c0 = 0; c0 < W; c0 += 32) {
+            const int j = c0 + lane;
+            bool unsettled = false;
+            if (j < W) {
+                int best = INT32_MAX, bk = -1;
+                const int o = rowbuf[j];
+                if (o != OFF_NONE) {
+                    best = o * o;
+                    bk = j;
+                }
+                int rr = 1;
+                for (; rr < DIRECT_ROW_CAP && rr * rr < best; ++rr) {
+                    if (j - rr >= 0) {
+                        const int ol = rowbuf[j - rr];
+                        if (ol != OFF_NONE && ol * ol + rr * rr < best) {
+                            best = ol * ol + rr * rr;
+                            bk = j - rr;
+                        }
+                    }
+                    if (j + rr < W) {
+                        const int orr = rowbuf[j + rr];
+                        if (orr != OFF_NONE && orr * orr + rr * rr <= best) {
+                            best = orr * orr + rr * rr;
+                            bk = j + rr;
+                        }
+                    }
+                }
+                unsettled = rr * rr < best && (j - rr >= 0 || j + rr < W);
+                if (!unsettled) {
+                    const int64_t q = (int64_t)i * W + j;
+                    const int v = bk < 0 ? INT32_MAX : best;
+                    if (D) D[q] = v;
+                    if (F) F[q] = bk < 0 ? -1 : (i + rowbuf[bk]) * W + bk;
+                    if (dist) dist[q] = sqrt_rn_int(v);
+                }
+            }
+            if (__any_sync(FULL, unsettled)) {
+                gave_up = true;
+                break;
+            }
+        }
+        __syncwarp();
+        if (gave_up) {
+            *abort = 1;
+            break;
+        }
+    }
+    sync();
+    return *abort == 0;
 }
 
 // Tensor maps for TMA row stores: the output viewed as [rows][W] with an
@@ -194,14 +290,24 @@ k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
     unsigned char* stage0 = smem + band2d_col_bytes(W);
     if (TMA) stage0 = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(stage0) + 127) & ~uintptr_t(127));
     const BandSmem sm = carve_band_smem(stage0 + (TMA ? NW * TMA_STAGE_BYTES : 0), NW, (1 << lg) >> 5);
+    __shared__ int s_abort;
     const bool second = (int)blockIdx.x >= nbl;
     const RowJob& J = second ? J1 : J0;
     const int b = band0 + (second ? (int)blockIdx.x - nbl : (int)blockIdx.x);
+    if (threadIdx.x == 0) s_abort = 0;
     stage_band(J.s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x, J.invert != 0);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    if (W <= DIRECT_ROW_W) {
+        // narrow rows: the direct search, unless some pixel's answer is far
+        short* rowbuf = reinterpret_cast<short*>(reinterpret_cast<unsigned char*>(sm.ctr) + 16) + warp * W;
+        if (rows2d_direct(sbits, supdn, b, H, W, J.D, J.F, J.dist, rowbuf, &s_abort, lane, warp, NW, BlockSync()))
+            return;
+        // the TMA stores below must land after the plain stores above
+        if (TMA) asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
     BandRow2D line;
     line.bits = sbits;
     line.updn = supdn;
@@ -249,7 +355,7 @@ static cudaError_t launch_rows(int H, int W, const RowJob& J0, const RowJob* J1,
         lg = band_seg_log2(W, max_nw);
         NW = (W + (1 << lg) - 1) >> lg;
         smem = band2d_smem(W, lg, NW) + (tma ? NW * TMA_STAGE_BYTES + 128 : 0);
-        if (smem <= 227 * 1024) break;
+        if (smem <= 227 * 1024 - 64) break;   // room for the static shared flag
     }
     if (nbl <= 0) return cudaSuccess;
     const RowJob j1 = J1 ? *J1 : J0;
@@ -300,7 +406,7 @@ void batch_row_geometry(int W, int lgmin, int& lg, int& NW, int& groups)
 
 __host__ __device__ static size_t batch_group_bytes(int W, int lg, int NW)
 {
-    return band2d_col_bytes(W) + band_smem_bytes(NW, (1 << lg) >> 5);
+    return band2d_col_bytes(W) + band_smem_bytes(NW, (1 << lg) >> 5) + direct_row_bytes(W, NW);
 }
 
 // Segment minimums the autotuner may choose for the rows2d phase (the
@@ -336,6 +442,7 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
+    __shared__ int s_abort[BATCH_K2_WARPS];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t total = hdr->k_total[PH];
@@ -362,8 +469,15 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
             unsigned char* sfull = reinterpret_cast<unsigned char*>(supdn + W);
             const BandSmem sm = carve_band_smem(base + band2d_col_bytes(W), NW, (1 << lg) >> 5);
             const GroupSync sync{1 + grp, NW * 32};
+            if (wg == 0 && lane == 0) s_abort[grp] = 0;
             stage_band(J.s, b, H, W, sbits, supdn, sfull, wg * 32 + lane, NW * 32);
             sync();
+            bool done = false;
+            if (W <= DIRECT_ROW_W) {
+                short* rowbuf = reinterpret_cast<short*>(reinterpret_cast<unsigned char*>(sm.ctr) + 16) + wg * W;
+                done = rows2d_direct(sbits, supdn, b, H, W, J.D, J.F, J.dist, rowbuf, &s_abort[grp], lane, wg, NW,
+                                     sync);
+            }
             BandRow2D line;
             line.bits = sbits;
             line.updn = supdn;
@@ -376,7 +490,7 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
             line.valid = line.i < H;
             const int vec = row_vec_width(W, J.D, J.F, J.dist);
             const RowOut out{J.D, J.F, J.dist, (int64_t)line.i * W, line.valid, vec};
-            band_envelope(line, out, sm, W, lg, NW, sfull, wg, sync);
+            if (!done) band_envelope(line, out, sm, W, lg, NW, sfull, wg, sync);
         }
         __syncthreads();
     }
@@ -421,11 +535,23 @@ int batch_wide_blocks_per_sm()
     return n;
 }
 
+// Opt a kernel in to all the dynamic shared memory a block may have beside
+// its static shared memory (227 KB per block in all).
+template <class K>
+static cudaError_t allow_max_dynamic_smem(K kernel)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(227 * 1024 - a.sharedSizeBytes));
+}
+
 cudaError_t set_2d_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_rows2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = allow_max_dynamic_smem(k_rows2d<true>);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_rows2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    return allow_max_dynamic_smem(k_rows2d<false>);
 }
 
 }  // namespace edt

@@ -94,6 +94,8 @@ inline cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t) { mem
 
 enum cudaFuncAttribute { cudaFuncAttributeMaxDynamicSharedMemorySize };
 template <class F> inline cudaError_t cudaFuncSetAttribute(F, cudaFuncAttribute, int) { return 0; }
+struct cudaFuncAttributes { size_t sharedSizeBytes = 0; };
+template <class F> inline cudaError_t cudaFuncGetAttributes(cudaFuncAttributes* a, F) { a->sharedSizeBytes = 0; return 0; }
 template <class F> inline cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int* n, F, int, size_t) { *n = 2; return 0; }
 typedef int cudaDriverEntryPointQueryResult;
 constexpr int cudaDriverEntryPointSuccess = 0;

@@ -379,8 +379,10 @@ def measure_volume(edt, torch, dev, reps=10):
 def measure_small(edt, torch, dev, calls=2000):
     """512 x 512 Bernoulli p = 0.01 image (seed 1), to object, D + F: one
     plain edt_feature call after another on one stream, launch-latency bound.
-    Per call: GPU time by CUDA events around the call, and host wall time of
-    the call (the library's own enqueue work, before synchronising)."""
+    Per call: GPU time by CUDA events around the call (this includes the
+    wait for the host's enqueue work), the device time alone (the call
+    captured in a CUDA graph and replayed), and host wall time of the call
+    (the library's own enqueue work, before synchronising)."""
     from paper_2106_03503_gb300 import inputs
     m = torch.from_numpy(inputs.points_512()).to(dev)
     D = torch.empty(m.shape, dtype=torch.int32, device=dev)
@@ -408,6 +410,35 @@ def measure_small(edt, torch, dev, calls=2000):
     back_to_back = 1e6 * (time.perf_counter() - t0) / calls
     gpu.sort()
     host.sort()
+    # device time alone: the same call captured once into a CUDA graph and
+    # replayed, events around each replay (the events above also count the
+    # host's enqueue work, which the GPU waits for)
+    dev_us = []
+    graph_note = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            edt.feature(m, 0, out=(D, F, None), stream=side)
+            side.synchronize()
+            with torch.cuda.graph(g, stream=side):
+                edt.feature(m, 0, out=(D, F, None), stream=side)
+        torch.cuda.synchronize()
+        for _ in range(20):
+            g.replay()
+        torch.cuda.synchronize()
+        for _ in range(calls):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            b.synchronize()
+            dev_us.append(1e3 * a.elapsed_time(b))
+        dev_us.sort()
+    except Exception as exc:  # noqa: BLE001
+        graph_note = f"graph capture unavailable: {exc!r}"[:200]
     import oracle
     small_np = inputs.points_512()
     cpu = oracle_beside(lambda: [oracle.edt(small_np, 0) for _ in range(10)], 10 * small_np.size,
@@ -416,6 +447,9 @@ def measure_small(edt, torch, dev, calls=2000):
     return {"workload": "2D 512x512 Bernoulli p=0.01 (seed 1), to object, D+F, plain edt_feature calls",
             "calls": calls, "gpu_us_p50": q(gpu, 0.5), "gpu_us_p99": q(gpu, 0.99),
             "host_enqueue_us_p50": q(host, 0.5), "host_enqueue_us_p99": q(host, 0.99),
+            "device_us_p50": q(dev_us, 0.5) if dev_us else None,
+            "device_us_p99": q(dev_us, 0.99) if dev_us else None,
+            "device_us_note": graph_note or "one captured call replayed as a CUDA graph, events around each replay",
             "back_to_back_us_per_call": back_to_back, "cpu_oracle": cpu,
             "gpx_s_back_to_back": m.numel() / (back_to_back * 1e-6) / 1e9}
 
@@ -851,12 +885,19 @@ def run_gpu(args, rank, world, local_rank):
 def run_profile_workload(edt, torch, dev, which: str, calls: int, jobs: int = 4096):
     """The kernels of one extra workload and nothing else, `calls` times, for
     ncu launch lists and captures: "nedt" = city-block and chamfer 4-3 of the
-    8192^2 discs mask, both source classes; "volume" / "volume256" = the 3-D
+    8192^2 discs mask, both source classes; "small" = the 512^2 points image
+    (to object, D + F); "volume" / "volume256" = the 3-D
     transform (to object, D + F) of the 512^3 / 256^3 smoothed-noise volume;
     "batch" = one edt_batch replay of the first `jobs` masks of the 4096-mask
     batch workload (to object, D + F)."""
     from paper_2106_03503_gb300 import inputs
-    if which == "batch":
+    if which == "small":
+        m = torch.from_numpy(inputs.points_512()).to(dev)
+        D = torch.empty(m.shape, dtype=torch.int32, device=dev)
+        F = torch.empty_like(D)
+        for _ in range(calls):
+            edt.feature(m, 0, out=(D, F, None))
+    elif which == "batch":
         masks = [torch.from_numpy(m).to(dev) for m in inputs.batch_4096()[:jobs]]
         outs = [(torch.empty(m.shape, dtype=torch.int32, device=dev),
                  torch.empty(m.shape, dtype=torch.int32, device=dev)) for m in masks]
@@ -895,7 +936,8 @@ def main():
                     help="skip the batch and serving measurements")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus --steps steps of the workload only (for ncu)")
-    ap.add_argument("--profile-workload", default="pair", choices=["pair", "nedt", "volume", "volume256", "batch"],
+    ap.add_argument("--profile-workload", default="pair",
+                    choices=["pair", "nedt", "volume", "volume256", "batch", "small"],
                     help="with --profile: the headline pair (default) or one extra workload, --steps calls")
     ap.add_argument("--profile-jobs", type=int, default=4096,
                     help="with --profile-workload batch: how many of the 4096 masks")

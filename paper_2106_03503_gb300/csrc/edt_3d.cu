@@ -156,7 +156,7 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, ui
                 const short* col = gz + lane;
                 const int d0 = col[j * 32];
                 int best = d0 * d0, bk = j;
-                for (int r = 1, r2 = 1; r2 < best; ++r, r2 += 2 * r - 1) {
+                for (int r = 1, r2 = 1; r2 <= best; ++r, r2 += 2 * r - 1) {
                     const int dl = col[(j - r) * 32], dr = col[(j + r) * 32];
                     const int cl = dl * dl + r2, cr = dr * dr + r2;
                     if (cl < best) { best = cl; bk = j - r; }
@@ -307,7 +307,7 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
                     best = own;
                     bk = j;
                 }
-                for (int r = 1; r < W && r * r < best; ++r) {
+                for (int r = 1; r < W && r * r <= best; ++r) {
                     if (j - r >= 0) {
                         const int c = cost(j - r);
                         if (c != INT32_MAX && c + r * r < best) {

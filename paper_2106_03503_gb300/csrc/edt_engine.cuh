@@ -603,8 +603,9 @@ __device__ void band_fill(const Line& line, const Out& out, const BandSmem& sm, 
 
 // Direct minimum for lines whose answers are near: position j takes the
 // minimum over k of f(k) + (j - k)^2 (Eq. (5)), searched outward from j,
-// r = 0, 1, 2, ..., until r^2 is no smaller than the best value found --
-// every k farther away costs at least r^2, so the result is exact.  At a tie
+// r = 0, 1, 2, ..., through the first r with r^2 above the best value found --
+// every k farther away costs more, so the result is exact, and a k at r^2
+// equal to the best (a source in the line itself) is still seen.  At a tie
 // the rightmost k is kept (a candidate left of the current best must be
 // strictly smaller, one right of it may tie), the same choice as the hull
 // walk of band_fill.  Each warp takes every NW-th chunk of OC positions of the
@@ -627,7 +628,7 @@ __device__ void band_direct(const Line& line, const Out& out, int n, int warp, i
                 best = f;
                 bk = j;
             }
-            for (int r = 1; r < n && r * r < best; ++r) {
+            for (int r = 1; r < n && r * r <= best; ++r) {
                 if (j - r >= 0 && line.eval(j - r, f) && f + r * r < best) {
                     best = f + r * r;
                     bk = j - r;

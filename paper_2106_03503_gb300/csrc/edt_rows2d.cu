@@ -182,7 +182,7 @@ __device__ bool rows2d_direct(const uint32_t* sbits, const uint32_t* supdn, int 
                     bk = j;
                 }
                 int rr = 1;
-                for (; rr < DIRECT_ROW_CAP && rr * rr < best; ++rr) {
+                for (; rr <= DIRECT_ROW_CAP && rr * rr <= best; ++rr) {
                     if (j - rr >= 0) {
                         const int ol = rowbuf[j - rr];
                         if (ol != OFF_NONE && ol * ol + rr * rr < best) {
@@ -198,7 +198,7 @@ __device__ bool rows2d_direct(const uint32_t* sbits, const uint32_t* supdn, int 
                         }
                     }
                 }
-                unsettled = rr * rr < best && (j - rr >= 0 || j + rr < W);
+                unsettled = rr * rr <= best && (j - rr >= 0 || j + rr < W);
                 if (!unsettled) {
                     const int64_t q = (int64_t)i * W + j;
                     const int v = bk < 0 ? INT32_MAX : best;
@@ -273,8 +273,10 @@ struct RowJob {
 
 // One block per band of 32 rows, bands band0 .. band0 + nbl - 1: blocks
 // [0, nbl) run job 0, blocks [nbl, 2 nbl) job 1 (when two transforms of one
-// mask are fused).
-template <bool TMA>
+// mask are fused).  NARROW (rows up to DIRECT_ROW_W): the direct row pass
+// first, the hull engine only for bands it gives up on; wider rows are
+// compiled without it.
+template <bool TMA, bool NARROW>
 __global__ void __launch_bounds__(512, 2)
 k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
          const __grid_constant__ CUtensorMap mD0, const __grid_constant__ CUtensorMap mF0,
@@ -290,23 +292,25 @@ k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
     unsigned char* stage0 = smem + band2d_col_bytes(W);
     if (TMA) stage0 = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(stage0) + 127) & ~uintptr_t(127));
     const BandSmem sm = carve_band_smem(stage0 + (TMA ? NW * TMA_STAGE_BYTES : 0), NW, (1 << lg) >> 5);
-    __shared__ int s_abort;
     const bool second = (int)blockIdx.x >= nbl;
     const RowJob& J = second ? J1 : J0;
     const int b = band0 + (second ? (int)blockIdx.x - nbl : (int)blockIdx.x);
-    if (threadIdx.x == 0) s_abort = 0;
-    stage_band(J.s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x, J.invert != 0);
-    __syncthreads();
-
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    if (W <= DIRECT_ROW_W) {
+    if constexpr (NARROW) {
+        __shared__ int s_abort;
+        if (threadIdx.x == 0) s_abort = 0;
+        stage_band(J.s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x, J.invert != 0);
+        __syncthreads();
         // narrow rows: the direct search, unless some pixel's answer is far
         short* rowbuf = reinterpret_cast<short*>(reinterpret_cast<unsigned char*>(sm.ctr) + 16) + warp * W;
         if (rows2d_direct(sbits, supdn, b, H, W, J.D, J.F, J.dist, rowbuf, &s_abort, lane, warp, NW, BlockSync()))
             return;
         // the TMA stores below must land after the plain stores above
         if (TMA) asm volatile("fence.proxy.async.global;" ::: "memory");
+    } else {
+        stage_band(J.s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x, J.invert != 0);
+        __syncthreads();
     }
     BandRow2D line;
     line.bits = sbits;
@@ -360,12 +364,19 @@ static cudaError_t launch_rows(int H, int W, const RowJob& J0, const RowJob* J1,
     if (nbl <= 0) return cudaSuccess;
     const RowJob j1 = J1 ? *J1 : J0;
     const unsigned blocks = (unsigned)(nbl * (J1 ? 2 : 1));
-    if (tma)
-        k_rows2d<true><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1], m[2],
-                                                          m[3], m[4], m[5]);
+    const bool narrow = W <= DIRECT_ROW_W;
+    if (tma && narrow)
+        k_rows2d<true, true><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1],
+                                                                m[2], m[3], m[4], m[5]);
+    else if (tma)
+        k_rows2d<true, false><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1],
+                                                                 m[2], m[3], m[4], m[5]);
+    else if (narrow)
+        k_rows2d<false, true><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1],
+                                                                 m[2], m[3], m[4], m[5]);
     else
-        k_rows2d<false><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1], m[2],
-                                                           m[3], m[4], m[5]);
+        k_rows2d<false, false><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1],
+                                                                  m[2], m[3], m[4], m[5]);
     return cudaGetLastError();
 }
 
@@ -549,9 +560,11 @@ static cudaError_t allow_max_dynamic_smem(K kernel)
 
 cudaError_t set_2d_attributes()
 {
-    cudaError_t e = allow_max_dynamic_smem(k_rows2d<true>);
-    if (e != cudaSuccess) return e;
-    return allow_max_dynamic_smem(k_rows2d<false>);
+    cudaError_t e = allow_max_dynamic_smem(k_rows2d<true, true>);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_rows2d<true, false>);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_rows2d<false, true>);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_rows2d<false, false>);
+    return e;
 }
 
 }  // namespace edt

@@ -25,6 +25,13 @@ Tuning edt::tuning_lookup(int, const int*) { return Tuning{}; }
 BatchTuning edt::batch_tuning_lookup(int, const int*) { return BatchTuning{}; }
 
 static uint64_t rng_state = 12345;
+// features that are valid but name a different nearest source than the
+// oracle's (both break ties the same way, so this should stay 0)
+static long long g_f_differs = 0;
+static void count_f(const int32_t* F, const std::vector<int32_t>& Fo, size_t n)
+{
+    for (size_t i = 0; i < n; ++i) g_f_differs += F[i] != Fo[i];
+}
 static double urand()
 {
     rng_state = rng_state * 6364136223846793005ULL + 1442695040888963407ULL;
@@ -88,6 +95,7 @@ static int run2d(int H, int W, double p, int mode, int align_off, bool pair)
         std::vector<int32_t> Do(n), Fo(n);
         oracle_edt2d(mask.data(), H, W, mm, Do.data(), Fo.data());
         bad += check_features(mask, H, W, mm, k ? D1 : D, k ? F1 : F, Do);
+        count_f(k ? F1 : F, Fo, (size_t)H * W);
         if (!pair)
             for (size_t i = 0; i < n && bad < 5; ++i) {
                 const float want = Do[i] == INT32_MAX ? INFINITY : (float)std::sqrt((double)Do[i]);
@@ -115,6 +123,7 @@ static int run3d(int Dz, int H, int W, double p, int mode)
     launch_xpass3d(Dz, H, W, reinterpret_cast<uint32_t*>(F), D, F, dist, nullptr);
     std::vector<int32_t> Do(n), Fo(n);
     oracle_edt3d(mask.data(), Dz, H, W, mode, Do.data(), Fo.data());
+    count_f(F, Fo, n);
     int bad = 0;
     for (size_t q = 0; q < n && bad < 5; ++q)
         if (D[q] != Do[q]) { fprintf(stderr, "3-D D mismatch %dx%dx%d at %zu: %d vs %d\n", Dz, H, W, q, D[q], Do[q]); ++bad; }
@@ -212,9 +221,11 @@ static int run_batch(int njobs, int blocks)
         if (j.ndim == 2) {
             oracle_edt2d(j.mask.data(), j.shape[0], j.shape[1], j.mode, Do.data(), Fo.data());
             bad += check_features(j.mask, j.shape[0], j.shape[1], j.mode, j.D, j.F, Do);
+            count_f(j.F, Fo, j.n);
         } else {
             oracle_edt3d(j.mask.data(), j.shape[0], j.shape[1], j.shape[2], j.mode, Do.data(), Fo.data());
             bad += check_features3d(j.mask, j.shape[0], j.shape[1], j.shape[2], j.mode, j.D, j.F, Do);
+            count_f(j.F, Fo, j.n);
         }
         free(j.D);
         free(j.F);
@@ -360,7 +371,7 @@ int main(int argc, char** argv)
                 bad += run_batch(njobs, blocks);
                 ++cases;
             }
-        printf("batch cases %d bad %d\n", cases, bad);
+        printf("batch cases %d bad %d f_differs %lld\n", cases, bad, g_f_differs);
         return bad != 0;
     }
     if (argc > 1 && !strcmp(argv[1], "3d")) {
@@ -374,7 +385,7 @@ int main(int argc, char** argv)
                     bad += run3d(sh[0], sh[1], sh[2], p, mode);
                     ++cases;
                 }
-        printf("3d cases %d bad %d\n", cases, bad);
+        printf("3d cases %d bad %d f_differs %lld\n", cases, bad, g_f_differs);
         return bad != 0;
     }
     const int part = argc > 3 ? atoi(argv[2]) : 0, nparts = argc > 3 ? atoi(argv[3]) : 1;
@@ -392,6 +403,6 @@ int main(int argc, char** argv)
                 bad += run2d(H, W, p, c & 1, (c % 3 == 0) ? 4 : ((c % 7 == 0) ? 1 : 0), c % 5 == 0);
             }
         }
-    printf("2d cases %d bad %d\n", run, bad);
+    printf("2d cases %d bad %d f_differs %lld\n", run, bad, g_f_differs);
     return bad != 0;
 }

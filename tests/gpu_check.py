@@ -33,6 +33,14 @@ def feature_valid_fast(mask, mode, D, F):
     return None
 
 
+def assert_same_features(F, Fo):
+    if not np.array_equal(F, Fo):
+        bad = np.argwhere(F != Fo)
+        i = tuple(bad[0])
+        raise AssertionError(f"F differs from the oracle's at {len(bad)} pixels, first {i}: "
+                             f"gpu {F[i]} oracle {Fo[i]}")
+
+
 def run_gpu(mask, mode, want_dist=True):
     from paper_2106_03503_gb300 import edt
     t = torch.from_numpy(np.ascontiguousarray(mask)).cuda()
@@ -41,15 +49,22 @@ def run_gpu(mask, mode, want_dist=True):
     return tuple(None if o is None else o.cpu().numpy() for o in out)
 
 
-def check_against_oracle(mask, mode, want_dist=True, ref=None):
+def check_against_oracle(mask, mode, want_dist=True, ref=None, ref_F=None):
     D, F, *rest = run_gpu(mask, mode, want_dist)
-    Do = oracle.edt(mask, mode)[0] if ref is None else ref
+    if ref is None:
+        Do, Fo = oracle.edt(mask, mode)
+    else:
+        Do, Fo = ref, ref_F
     if not np.array_equal(D, Do):
         bad = np.argwhere(D != Do)
         i = tuple(bad[0])
         raise AssertionError(f"D mismatch at {len(bad)} pixels, first {i}: gpu {D[i]} oracle {Do[i]}")
     msg = feature_valid_fast(mask, mode, D, F)
     assert msg is None, msg
+    if Fo is not None:
+        # the same nearest source as the oracle: both keep the rightmost column
+        # at an integer intersection (Eq. (6)) and the upper source in a column
+        assert_same_features(F, Fo)
     if want_dist:
         dist = rest[0]
         assert np.array_equal(dist.view(np.uint32), oracle.sqrt_f32(Do).view(np.uint32)), "sqrt mismatch"

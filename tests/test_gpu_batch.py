@@ -36,12 +36,13 @@ def _check(jobs, refs, torch):
     for k, ((m, mode, D, F, dist), (Dr, Fr, dr)) in enumerate(zip(jobs, refs)):
         # against the oracle
         m_np = m.cpu().numpy()
-        Do, _ = oracle.edt(m_np, mode)
+        Do, Fo = oracle.edt(m_np, mode)
         F_np = F.cpu().numpy()
         if D is not None:
             assert np.array_equal(D.cpu().numpy(), Do), k
         msg = feature_valid_fast(m_np, mode, Do, F_np)
         assert msg is None, (k, msg)
+        assert np.array_equal(F_np, Fo), (k, "F differs from the oracle's")
         if dist is not None:
             assert np.array_equal(dist.cpu().numpy().view(np.uint32), oracle.sqrt_f32(Do).view(np.uint32)), k
         # and bit-identical to the plain call
@@ -203,8 +204,9 @@ def test_full_batch_workload_4096():
         D, F = outs[k]
         assert torch.equal(D, Dr) and torch.equal(F, Fr), k
     for k in range(0, len(masks), 128):
-        Do, _ = oracle.edt(masks_np[k], 0)
+        Do, Fo = oracle.edt(masks_np[k], 0)
         D, F = outs[k]
         D, F = D.cpu().numpy(), F.cpu().numpy()
         assert np.array_equal(D, Do), k
         assert feature_valid_fast(masks_np[k], 0, D, F) is None
+        assert np.array_equal(F, Fo), k

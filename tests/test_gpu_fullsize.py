@@ -32,15 +32,17 @@ def test_discs_8192_pair_as_benchmarked():
     column pass and one row launch for both transforms); D equal to the
     oracle on every pixel of both transforms, F a nearest source."""
     import torch
-    from gpu_check import feature_valid_fast
+    from gpu_check import assert_same_features, feature_valid_fast
     from paper_2106_03503_gb300 import edt
     m_np = inputs.discs_8192()
     (Do, Fo), (Db, Fb) = edt.feature_pair(torch.from_numpy(m_np).cuda())
     torch.cuda.synchronize()
     for mode, (D, F) in ((0, (Do, Fo)), (1, (Db, Fb))):
         D, F = D.cpu().numpy(), F.cpu().numpy()
-        np.testing.assert_array_equal(D, oracle.edt(m_np, mode)[0])
+        D_or, F_or = oracle.edt(m_np, mode)
+        np.testing.assert_array_equal(D, D_or)
         assert feature_valid_fast(m_np, mode, D, F) is None
+        assert_same_features(F, F_or)
 
 
 def test_discs_8192_pair_host_as_benchmarked():
@@ -49,9 +51,12 @@ def test_discs_8192_pair_host_as_benchmarked():
     import torch
     from paper_2106_03503_gb300 import edt
     m_np = inputs.discs_8192()
+    from gpu_check import assert_same_features
     (Do, Fo), (Db, Fb) = edt.feature_pair_host(torch.from_numpy(m_np).pin_memory())
-    np.testing.assert_array_equal(Do.numpy(), oracle.edt(m_np, 0)[0])
-    np.testing.assert_array_equal(Db.numpy(), oracle.edt(m_np, 1)[0])
+    for mode, (D, F) in ((0, (Do, Fo)), (1, (Db, Fb))):
+        D_or, F_or = oracle.edt(m_np, mode)
+        np.testing.assert_array_equal(D.numpy(), D_or)
+        assert_same_features(F.numpy(), F_or)
 
 
 def _sparse_sources_check(shape, n_src, seed, mode):

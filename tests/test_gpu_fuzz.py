@@ -37,13 +37,15 @@ def mask2d(rng):
 
 
 def check(name, m, mode, D, F=None, dist=None):
-    Do = oracle.edt(m, mode)[0]
+    Do, Fo = oracle.edt(m, mode)
     if not np.array_equal(D, Do):
         raise AssertionError(f"{name}: D mismatch at {int((D != Do).sum())} px")
     if F is not None:
         msg = feature_valid_fast(m, mode, D, F)
         if msg:
             raise AssertionError(f"{name}: {msg}")
+        if not np.array_equal(F, Fo):   # the oracle breaks ties the same way
+            raise AssertionError(f"{name}: F differs from the oracle's at {int((F != Fo).sum())} px")
     if dist is not None and not np.array_equal(dist.view(np.uint32), oracle.sqrt_f32(Do).view(np.uint32)):
         raise AssertionError(f"{name}: sqrt mismatch")
 

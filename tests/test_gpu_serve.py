@@ -81,12 +81,13 @@ def test_alone_equals_in_the_mix_equals_plain():
         # the oracle decides: every served D bit-exact, F a nearest source,
         # dist the correctly rounded square root
         m_np = masks[k].numpy()
-        Do, _ = oracle.edt(m_np, k % 2)
+        Do, Fo = oracle.edt(m_np, k % 2)
         for D, F, d in (alone[k], mix[k]):
             D, F, d = D.numpy(), F.numpy(), d.numpy()
             assert np.array_equal(D, Do), k
             msg = feature_valid_fast(m_np, k % 2, D, F)
             assert msg is None, (k, msg)
+            assert np.array_equal(F, Fo), (k, "F differs from the oracle's")
             assert np.array_equal(d.view(np.uint32), oracle.sqrt_f32(Do).view(np.uint32)), k
         # and the same bits alone, in the mix and from a plain call
         for a, b, c in zip(plain[k], alone[k], mix[k]):

@@ -5,7 +5,8 @@ the library's own table builder) compiled as C++ and run on the CPU by a
 host emulation (tests/emu): one fiber per CUDA thread, barriers and warp
 collectives emulated, dynamic shared memory allocated at exactly the
 launch's size under AddressSanitizer.  The results must equal the oracle's
-(D exactly, F a nearest source, dist correctly rounded).  This checks the
+(D exactly, F a nearest source -- and the same one the oracle names, since
+both break ties the same way -- dist correctly rounded).  This checks the
 kernels' index arithmetic, shared-memory carving, store alignment and
 warp-collective discipline before they run on a GPU; it is test
 infrastructure and never part of the library."""
@@ -63,6 +64,10 @@ def _run_all(cmds):
     for p, (o, e) in zip(procs, outs):
         errs = "\n".join(ln for ln in e.splitlines() if "makecontext/swapcontext" not in ln)
         assert p.returncode == 0 and " bad 0" in o, f"{o}\n{errs[-4000:]}"
+        # the kernels break ties as the oracle does (rightmost column at an
+        # integer intersection, upper source in a column): F is the oracle's
+        if "f_differs" in o:
+            assert " f_differs 0" in o, o
 
 
 def test_kernels_2d_match_oracle(emu):

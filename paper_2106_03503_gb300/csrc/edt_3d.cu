@@ -291,46 +291,42 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
             const int64_t row = row0 + rl;
             if (row >= nrows) break;
             const int zz = (int)(row / H), yy = (int)(row % H);
-            const uint32_t* rr = rec + rl * pitch;
+            uint32_t* rr = rec + rl * pitch;
+            // the warp's own row, rewritten in place: bits 31..24 and 23..16
+            // the z and y offsets of the record (each within +-64 here), bits
+            // 15..0 their squared length (at most 2 * 64^2), so that a
+            // candidate costs one load and a mask
+            for (int k = lane; k < W; k += 32) {
+                const uint32_t p = rr[k];
+                const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
+                rr[k] = ((uint32_t)(dz & 0xFF) << 24) | ((uint32_t)(dy & 0xFF) << 16) | (uint32_t)(dz * dz + dy * dy);
+            }
+            __syncwarp();
             for (int c0 = 0; c0 < W; c0 += 32) {
                 const int j = c0 + lane;
                 if (j >= W) continue;
-                int best = INT32_MAX, bk = -1;
-                auto cost = [&](int k) -> int {   // (z, y) squared distance of column k's record
-                    const uint32_t p = rr[k];
-                    if (p == PNONE) return INT32_MAX;
-                    const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
-                    return dz * dz + dy * dy;
-                };
-                const int own = cost(j);
-                if (own != INT32_MAX) {
-                    best = own;
-                    bk = j;
-                }
-                for (int r = 1; r < W && r * r <= best; ++r) {
+                int best = (int)(rr[j] & 0xFFFFu), bk = j;
+                for (int r = 1, r2 = 1; r2 <= best; ++r, r2 += 2 * r - 1) {
                     if (j - r >= 0) {
-                        const int c = cost(j - r);
-                        if (c != INT32_MAX && c + r * r < best) {
-                            best = c + r * r;
+                        const int c = (int)(rr[j - r] & 0xFFFFu) + r2;
+                        if (c < best) {
+                            best = c;
                             bk = j - r;
                         }
                     }
                     if (j + r < W) {
-                        const int c = cost(j + r);
-                        if (c != INT32_MAX && c + r * r <= best) {
-                            best = c + r * r;
+                        const int c = (int)(rr[j + r] & 0xFFFFu) + r2;
+                        if (c <= best) {
+                            best = c;
                             bk = j + r;
                         }
                     }
                 }
+                const uint32_t p = rr[bk];
+                const int dz = (int)(int8_t)(p >> 24), dy = (int)(int8_t)((p >> 16) & 0xFFu);
                 const int64_t q = row * W + j;
-                int f = -1;
-                if (bk >= 0) {
-                    const uint32_t p = rr[bk];
-                    f = (((int)(p >> 16) * H) + (int)(p & 0xFFFFu)) * W + bk;
-                }
                 if (D) D[q] = best;
-                if (F) F[q] = f;
+                if (F) F[q] = ((zz - dz) * H + (yy - dy)) * W + bk;
                 if (dist) dist[q] = sqrt_rn_int(best);
             }
         }

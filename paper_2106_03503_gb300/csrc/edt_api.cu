@@ -77,6 +77,13 @@ edt_status device_setup(int* sm_count)
     return EDT_OK;
 }
 
+int device_sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    return g_dev[dev].ready.load(std::memory_order_acquire) ? g_dev[dev].sm_count : 0;
+}
+
 // Shape checks shared by every entry point (limits documented in edt.h).
 // Copy stream of the current device (device_setup must have run).
 static cudaStream_t copy_stream()

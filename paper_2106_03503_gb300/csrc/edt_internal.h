@@ -196,6 +196,8 @@ Tuning tuning_lookup(int ndim, const int* shape);
 void tuning_store(int ndim, const int* shape, const Tuning& t);
 
 cudaError_t set_2d_attributes();
+// SM count of the current device (cached by the per-device set-up; 0 before it)
+int device_sm_count();
 cudaError_t set_chamfer_attributes();
 cudaError_t set_3d_attributes();
 

@@ -148,16 +148,17 @@ __device__ __forceinline__ void stage_band(const ColScratch& s, int b, int H, in
 // and writes whole 128-byte lines of D, F and dist.  A search that reaches
 // DIRECT_ROW_CAP columns with candidates left gives up for the whole band
 // (abort flag): the caller then runs the hull engine, which rewrites every
-// pixel with the same value.  Called by the nthr threads of one engine, which
-// must have cleared *abort before their last barrier; returns true when the
-// band is done (the same answer in every thread).
+// pixel with the same value.  Only the band's rows rlo .. rhi - 1 are done.
+// Called by the nthr threads of one engine, which must have cleared *abort
+// before their last barrier; returns true when those rows are done (the same
+// answer in every thread).
 template <class Sync>
 __device__ bool rows2d_direct(const uint32_t* sbits, const uint32_t* supdn, int b, int H, int W, int32_t* D,
                               int32_t* F, float* dist, short* rowbuf, volatile int* abort, int lane, int warp,
-                              int NW, Sync sync)
+                              int NW, Sync sync, int rlo = 0, int rhi = 32)
 {
-    const int base = b * 32, rows = min(32, H - base);
-    for (int r = warp; r < rows; r += NW) {
+    const int base = b * 32, rows = min(rhi, H - base);
+    for (int r = rlo + warp; r < rows; r += NW) {
         if (*abort) break;
         const int i = base + r;
         const uint32_t mle = FULL >> (31 - r), mge = FULL << r;
@@ -278,7 +279,7 @@ struct RowJob {
 // compiled without it.
 template <bool TMA, bool NARROW>
 __global__ void __launch_bounds__(512, 2)
-k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
+k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW, int split,
          const __grid_constant__ CUtensorMap mD0, const __grid_constant__ CUtensorMap mF0,
          const __grid_constant__ CUtensorMap mS0, const __grid_constant__ CUtensorMap mD1,
          const __grid_constant__ CUtensorMap mF1, const __grid_constant__ CUtensorMap mS1)
@@ -292,9 +293,13 @@ k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
     unsigned char* stage0 = smem + band2d_col_bytes(W);
     if (TMA) stage0 = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(stage0) + 127) & ~uintptr_t(127));
     const BandSmem sm = carve_band_smem(stage0 + (TMA ? NW * TMA_STAGE_BYTES : 0), NW, (1 << lg) >> 5);
-    const bool second = (int)blockIdx.x >= nbl;
+    // `split` blocks share a band (small images: more blocks than bands),
+    // block `part` of them doing rows part * 32 / split onwards
+    const int bi = (int)blockIdx.x / split, part = (int)blockIdx.x - bi * split;
+    const int rlo = part * (32 / split), rhi = rlo + 32 / split;
+    const bool second = bi >= nbl;
     const RowJob& J = second ? J1 : J0;
-    const int b = band0 + (second ? (int)blockIdx.x - nbl : (int)blockIdx.x);
+    const int b = band0 + (second ? bi - nbl : bi);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     if constexpr (NARROW) {
@@ -304,7 +309,8 @@ k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
         __syncthreads();
         // narrow rows: the direct search, unless some pixel's answer is far
         short* rowbuf = reinterpret_cast<short*>(reinterpret_cast<unsigned char*>(sm.ctr) + 16) + warp * W;
-        if (rows2d_direct(sbits, supdn, b, H, W, J.D, J.F, J.dist, rowbuf, &s_abort, lane, warp, NW, BlockSync()))
+        if (rows2d_direct(sbits, supdn, b, H, W, J.D, J.F, J.dist, rowbuf, &s_abort, lane, warp, NW, BlockSync(),
+                          rlo, rhi))
             return;
         // the TMA stores below must land after the plain stores above
         if (TMA) asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -329,7 +335,8 @@ k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
         band_envelope(line, out, sm, W, lg, NW, sfull);
     } else {
         const int vec = row_vec_width(W, J.D, J.F, J.dist);
-        const RowOut out{J.D, J.F, J.dist, (int64_t)line.i * W, line.valid, vec};
+        // with a split band, this block writes its own rows only
+        const RowOut out{J.D, J.F, J.dist, (int64_t)line.i * W, line.valid && lane >= rlo && lane < rhi, vec};
         band_envelope(line, out, sm, W, lg, NW, sfull);
     }
 }
@@ -363,20 +370,29 @@ static cudaError_t launch_rows(int H, int W, const RowJob& J0, const RowJob* J1,
     }
     if (nbl <= 0) return cudaSuccess;
     const RowJob j1 = J1 ? *J1 : J0;
-    const unsigned blocks = (unsigned)(nbl * (J1 ? 2 : 1));
     const bool narrow = W <= DIRECT_ROW_W;
+    // a small image's few bands are split over up to 4 blocks each (rows of a
+    // band divided among them, plain stores), so that more SMs share the work
+    int split = 1;
+    const int bands = nbl * (J1 ? 2 : 1);
+    if (narrow && device_sm_count() >= 2 * bands) {
+        split = min(4, device_sm_count() / bands);
+        split = split >= 4 ? 4 : (split >= 2 ? 2 : 1);
+        tma = false;
+    }
+    const unsigned blocks = (unsigned)(bands * split);
     if (tma && narrow)
-        k_rows2d<true, true><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1],
-                                                                m[2], m[3], m[4], m[5]);
+        k_rows2d<true, true><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, split, m[0],
+                                                                m[1], m[2], m[3], m[4], m[5]);
     else if (tma)
-        k_rows2d<true, false><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1],
-                                                                 m[2], m[3], m[4], m[5]);
+        k_rows2d<true, false><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, split, m[0],
+                                                                 m[1], m[2], m[3], m[4], m[5]);
     else if (narrow)
-        k_rows2d<false, true><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1],
-                                                                 m[2], m[3], m[4], m[5]);
+        k_rows2d<false, true><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, split, m[0],
+                                                                 m[1], m[2], m[3], m[4], m[5]);
     else
-        k_rows2d<false, false><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, m[0], m[1],
-                                                                  m[2], m[3], m[4], m[5]);
+        k_rows2d<false, false><<<blocks, NW * 32, smem, stream>>>(H, W, band0, nbl, J0, j1, lg, NW, split, m[0],
+                                                                  m[1], m[2], m[3], m[4], m[5]);
     return cudaGetLastError();
 }
 

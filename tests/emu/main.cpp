@@ -23,6 +23,8 @@ using namespace edt;
 // built-in geometry rules apply here.
 Tuning edt::tuning_lookup(int, const int*) { return Tuning{}; }
 BatchTuning edt::batch_tuning_lookup(int, const int*) { return BatchTuning{}; }
+// As many SMs as a GB300 has: small images take the split row launch here too.
+int edt::device_sm_count() { return 152; }
 
 static uint64_t rng_state = 12345;
 // features that are valid but name a different nearest source than the

@@ -142,7 +142,7 @@ void batch_line_geometry(int n, int pos, int& lg, int& NW);
 size_t batch_ypass_group_bytes(int H, int lg, int NW);
 size_t batch_xpass_group_bytes(int W, int lg, int NW);
 
-// Job table of one batch (edt_batch_table.cpp).  batch_kind: the job's kind,
+// Job table of one batch (edt_batch_table.cu).  batch_kind: the job's kind,
 // or -1 when it cannot be batched (`why` then says so).  batch_layout: the
 // column-pass scratch bytes and counter words a batch needs.  batch_fill: the
 // table (jobs ordered by kind, the heaviest first within a kind), with the

@@ -24,41 +24,46 @@ constexpr uint32_t PNONE = 0xFFFFFFFFu;
 // --- y pass ----------------------------------------------------------------
 
 // y tile data: for each (y, x), d = nearest source z along z minus z (int16,
-// YNONE when the column has no source), [YPAD + H + YPAD][32], the pads
-// holding YNONE so that a search may step past either end.
+// YNONE when the column has no source), [YPAD + H + YPAD] rows of YP entries
+// (32 used), the pads holding YNONE so that a search may step past either end.
+// A row is YP = 40 entries (20 words) apart, so that the 4 x 8 (y, x) patch of
+// a warp in the direct search reads 4 rows on disjoint groups of banks (rows
+// y .. y+3 start at banks 20y + {0, 20, 8, 28} mod 32), and the 32 lanes of
+// one row still read 16 consecutive words.
 constexpr short YNONE = 32767;
-constexpr int YPAD = DIRECT_MAX_DIST;
+constexpr int YPAD = DIRECT_MAX_DIST + 2;   // the search below looks one step past its stop
+constexpr int YP = 40;
 
 struct LineY {
-    const short* gz;         // row y' of this tile at gz[y' * 32] (pads around)
+    const short* gz;         // row y' of this tile at gz[y' * YP] (pads around)
     int lane;
     int z;
     __device__ __forceinline__ bool eval(int k, int& f) const
     {
-        const int d = gz[k * 32 + lane];
+        const int d = gz[k * YP + lane];
         if (d == YNONE) return false;
         f = d * d;
         return true;
     }
     __device__ __forceinline__ int c(int k) const
     {
-        const int d = gz[k * 32 + lane];
+        const int d = gz[k * YP + lane];
         return d * d + k * k;
     }
     __device__ __forceinline__ bool eval2(int k, int& f, int& feat) const
     {
-        const int d = gz[k * 32 + lane];
+        const int d = gz[k * YP + lane];
         if (d == YNONE) return false;
         f = d * d;
         feat = (int)(((uint32_t)(z + d) << 16) | (uint32_t)k);
         return true;
     }
-    __device__ __forceinline__ bool is_zero(int k) const { return gz[k * 32 + lane] == 0; }
+    __device__ __forceinline__ bool is_zero(int k) const { return gz[k * YP + lane] == 0; }
     __device__ __forceinline__ bool chunk_has_source(int j0) const
     {
         bool any = false;
 #pragma unroll
-        for (int t = 0; t < OC; ++t) any |= gz[(j0 + t) * 32 + lane] == 0;
+        for (int t = 0; t < OC; ++t) any |= gz[(j0 + t) * YP + lane] == 0;
         return any;
     }
     __device__ __forceinline__ int self_feature(int k) const
@@ -81,11 +86,11 @@ struct OutY {
     }
 };
 
-// y tile: z offsets of [YPAD + H + YPAD][32] (int16), per-warp maxima (32
+// y tile: z offsets of [YPAD + H + YPAD][YP] (int16), per-warp maxima (32
 // ints), engine
 __host__ __device__ static inline size_t ytile_bytes(int H)
 {
-    return ((size_t)(H + 2 * YPAD) * 32 * 2 + 15) & ~size_t(15);
+    return ((size_t)(H + 2 * YPAD) * YP * 2 + 15) & ~size_t(15);
 }
 __host__ __device__ static inline size_t ypass_smem(int H, int lg, int NW)
 {
@@ -101,7 +106,7 @@ template <class Sync>
 __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, uint32_t* __restrict__ P,
                            int z, int x0, unsigned char* base, int tid, int nthr, int warp, Sync sync)
 {
-    short* gz = reinterpret_cast<short*>(base) + YPAD * 32;     // row 0 of the tile
+    short* gz = reinterpret_cast<short*>(base) + YPAD * YP;     // row 0 of the tile
     int* wmax = reinterpret_cast<int*>(base + ytile_bytes(H));
     const BandSmem sm = carve_band_smem(base + ytile_bytes(H) + 128, NW, (1 << lg) >> 5);
     const int lane = tid & 31;
@@ -110,64 +115,88 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, ui
 
     // z offset of the nearest source along z of every (y, x) of the tile, and
     // the largest distance among them (columns past the volume's edge count
-    // as 0); the pads hold YNONE
+    // as 0); the pads hold YNONE.  Each thread first loads the column words
+    // of SU elements, then decodes them, so that SU pairs of loads are in
+    // flight at once.
+    for (int e = tid; e < YPAD * YP; e += nthr) {
+        gz[e - YPAD * YP] = YNONE;
+        gz[H * YP + e] = YNONE;
+    }
+    const uint32_t* Cz = s.C + (int64_t)zb * plane;
+    const uint32_t* Uz = s.U + (int64_t)zb * plane;
+    const int total = H * 32;
+    constexpr int SU = 4;
     int dmax = 0;
-    for (int e = tid; e < (H + 2 * YPAD) * 32; e += nthr) {
-        const int y = (e >> 5) - YPAD, xl = e & 31, x = x0 + xl;
-        int d = YNONE;
-        if (y >= 0 && y < H && x < W) {
-            const int64_t p = (int64_t)y * W + x;
-            const uint32_t w = s.C[(int64_t)zb * plane + p];
-            const uint32_t u = s.U[(int64_t)zb * plane + p];
-            uint32_t up = u & 0xFFFFu, dn = u >> 16;
-            if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
-                const uint32_t gab = s.GAB[(int64_t)zG * plane + p];
-                if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
-                if (dn == (uint32_t)NONE16) dn = gab >> 16;
+    for (int e0 = tid; e0 < total; e0 += SU * nthr) {
+        uint32_t w[SU], u[SU];
+#pragma unroll
+        for (int i = 0; i < SU; ++i) {
+            const int e = e0 + i * nthr, x = x0 + (e & 31);
+            w[i] = 0u;
+            u[i] = 0u;
+            if (e < total && x < W) {
+                const int64_t p = (int64_t)(e >> 5) * W + x;
+                w[i] = __ldg(Cz + p);
+                u[i] = __ldg(Uz + p);
             }
-            const int g = nearest_in_column(w, zb * 32, zr, (int)up, (int)dn);
-            d = g < 0 ? YNONE : g - z;
-            dmax = max(dmax, abs(d));
         }
-        gz[e - YPAD * 32] = (short)d;
+#pragma unroll
+        for (int i = 0; i < SU; ++i) {
+            const int e = e0 + i * nthr, x = x0 + (e & 31);
+            if (e >= total) break;
+            int d = YNONE;
+            if (x < W) {
+                uint32_t up = u[i] & 0xFFFFu, dn = u[i] >> 16;
+                if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
+                    const uint32_t gab = s.GAB[(int64_t)zG * plane + (int64_t)(e >> 5) * W + x];
+                    if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
+                    if (dn == (uint32_t)NONE16) dn = gab >> 16;
+                }
+                const int g = nearest_in_column(w[i], zb * 32, zr, (int)up, (int)dn);
+                d = g < 0 ? YNONE : g - z;
+                dmax = max(dmax, abs(d));
+            }
+            gz[(e >> 5) * YP + (e & 31)] = (short)d;
+        }
     }
     dmax = (int)__reduce_max_sync(FULL, (unsigned)dmax);
     if (lane == 0) wmax[warp] = dmax;
     sync();
     for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
 
-    const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
     if (dmax <= DIRECT_MAX_DIST) {
         // near answers: each position searches outward along y (Eq. (5)
-        // minimised exactly, rightmost y' at a tie, as the hull walk); every
-        // own offset is at most DIRECT_MAX_DIST = YPAD, so the search never
-        // leaves the padded tile and needs no bounds or validity test (a pad
-        // or a column without source costs 32767^2, more than any answer)
-        const int nq = (H + OC - 1) / OC;
-        for (int q = warp; q < nq; q += NW) {
-            const int j0 = q * OC;
-            int v[OC], ft[OC];
-#pragma unroll
-            for (int t = 0; t < OC; ++t) {
-                const int j = j0 + t;
-                v[t] = INT32_MAX;
-                ft[t] = -1;
-                if (j >= H || x0 + lane >= W) continue;   // not a voxel of the tile
-                const short* col = gz + lane;
-                const int d0 = col[j * 32];
-                int best = d0 * d0, bk = j;
-                for (int r = 1, r2 = 1; r2 <= best; ++r, r2 += 2 * r - 1) {
-                    const int dl = col[(j - r) * 32], dr = col[(j + r) * 32];
-                    const int cl = dl * dl + r2, cr = dr * dr + r2;
-                    if (cl < best) { best = cl; bk = j - r; }
-                    if (cr <= best) { best = cr; bk = j + r; }
-                }
-                v[t] = best;
-                ft[t] = (int)(((uint32_t)(z + col[bk * 32]) << 16) | (uint32_t)bk);
+        // minimised exactly, rightmost y' at a tie, as the hull walk), two
+        // steps per test of the stop rule (a step past the stop costs at least
+        // its r^2, more than the best, and changes nothing); every own offset
+        // is at most DIRECT_MAX_DIST, so the search stops by r = DIRECT_MAX_DIST
+        // + 1 < YPAD, never leaves the padded tile and needs no bounds or
+        // validity test (a pad or a column without source costs 32767^2, more
+        // than any answer).  A warp takes patches of 4 y x 8 x: a search runs
+        // as far as the farthest lane of its warp, and neighbours in both
+        // directions need more alike distances than 32 along x alone.
+        const int items = 4 * ((H + 3) >> 2);
+        for (int it = warp; it < items; it += NW) {
+            const int j = 4 * (it >> 2) + (lane >> 3), xt = 8 * (it & 3) + (lane & 7);
+            if (j >= H || x0 + xt >= W) continue;   // not a voxel of the tile
+            const short* col = gz + xt;
+            const int d0 = col[j * YP];
+            int best = d0 * d0, bk = j;
+            for (int r = 1, r2 = 1; r2 <= best; r += 2, r2 += 4 * r - 4) {
+                const int r2b = r2 + 2 * r + 1;
+                const int dl = col[(j - r) * YP], dr = col[(j + r) * YP];
+                const int dl2 = col[(j - r - 1) * YP], dr2 = col[(j + r + 1) * YP];
+                const int cl = dl * dl + r2, cr = dr * dr + r2;
+                const int cl2 = dl2 * dl2 + r2b, cr2 = dr2 * dr2 + r2b;
+                if (cl < best) { best = cl; bk = j - r; }
+                if (cr <= best) { best = cr; bk = j + r; }
+                if (cl2 < best) { best = cl2; bk = j - r - 1; }
+                if (cr2 <= best) { best = cr2; bk = j + r + 1; }
             }
-            out.store(j0, min(OC, H - j0), v, ft);
+            P[(int64_t)z * plane + (int64_t)j * W + x0 + xt] = ((uint32_t)(z + col[bk * YP]) << 16) | (uint32_t)bk;
         }
     } else {
+        const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
         const LineY line{gz, lane, z};
         band_envelope(line, out, sm, H, lg, NW, nullptr, warp, sync);
     }
@@ -227,13 +256,19 @@ struct LineX {
     __device__ __forceinline__ int self_feature(int k) const { return (z * H + y) * W + k; }
 };
 
-__host__ __device__ static inline int xpass_pitch(int W) { return W | 1; }
-
-// x unit: records of [32][pitch], per-warp maxima (32 ints), engine
+// x unit: the records of its 32 rows, row rl at XPAD + rl * pitch words, the
+// pitch odd (lane = row reads of the hull engine hit distinct banks) and at
+// least W + XPAD, so that XPAD words of pad lie before every row and after the
+// last; then per-warp maxima (32 ints) and the engine.
+constexpr int XPAD = 96;
+__host__ __device__ static inline int xpass_pitch(int W) { return (W + XPAD) | 1; }
+__host__ __device__ static inline size_t xpass_rec_bytes(int W)
+{
+    return ((size_t)(XPAD + 32 * xpass_pitch(W)) * 4 + 15) & ~size_t(15);
+}
 __host__ __device__ static inline size_t xpass_smem(int W, int lg, int NW)
 {
-    return (((size_t)32 * xpass_pitch(W) * 4 + 15) & ~size_t(15)) + 128 +
-           band_smem_bytes(NW, (1 << lg) >> 5);
+    return xpass_rec_bytes(W) + 128 + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
 size_t batch_xpass_group_bytes(int W, int lg, int NW) { return xpass_smem(W, lg, NW); }
@@ -244,36 +279,51 @@ template <class Sync>
 __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D, int32_t* F,
                            float* dist, int64_t row0, unsigned char* base, int tid, int nthr, int warp, Sync sync)
 {
-    const int pitch = W | 1;
-    uint32_t* rec = reinterpret_cast<uint32_t*>(base);   // [32][pitch]
-    int* wmax = reinterpret_cast<int*>(base + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)));
-    const BandSmem sm = carve_band_smem(base + (((size_t)32 * pitch * 4 + 15) & ~size_t(15)) + 128, NW,
-                                        (1 << lg) >> 5);
+    const int pitch = xpass_pitch(W);
+    uint32_t* rec = reinterpret_cast<uint32_t*>(base) + XPAD;   // row rl at rec[rl * pitch]
+    int* wmax = reinterpret_cast<int*>(base + xpass_rec_bytes(W));
+    const BandSmem sm = carve_band_smem(base + xpass_rec_bytes(W) + 128, NW, (1 << lg) >> 5);
     const int lane = tid & 31;
     const int64_t nrows = (int64_t)Dz * H;
 
+    // the pads (before row 0 and after every row) cost 0xFFFF to the direct
+    // search below, more than any answer it accepts
+    for (int t = tid; t < 33 * (XPAD + 1); t += nthr) {
+        const int g = t / (XPAD + 1), o = t - g * (XPAD + 1);
+        const int start = g == 0 ? -XPAD : (g - 1) * pitch + W;
+        const int end = g == 0 ? 0 : (g == 32 ? 31 * pitch + W + XPAD : g * pitch);
+        if (start + o < end) rec[start + o] = 0xFFFFu;
+    }
     // the rows' (z', y') records, and the largest (z, y) distance among them
-    // (rows past the volume's end count as 0); (z, y) of the unit's first row
-    // once, then stepped row by row, so the loads need no divisions
+    // (rows past the volume's end count as 0); the (z, y) of RU rows at a time
+    // stepped from the unit's first, so the loads need no divisions, and RU
+    // loads in flight per thread
+    constexpr int RU = 4;
     int dmax = 0;
-    int zz = (int)(row0 / H), yy = (int)(row0 % H);
-    for (int rl = 0; rl < 32; ++rl) {
-        const int64_t row = row0 + rl;
-        const bool live = row < nrows;
-        const uint32_t* src = P + row * W;
-        uint32_t* dst = rec + rl * pitch;
-        for (int k = tid; k < W; k += nthr) {
-            uint32_t p = PNONE;
-            if (live) {
-                p = src[k];
-                const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
-                dmax = max(dmax, p == PNONE ? 32767 : max(abs(dz), abs(dy)));
+    int zn = (int)(row0 / H), yn = (int)(row0 % H);
+    for (int rl0 = 0; rl0 < 32; rl0 += RU) {
+        int zr[RU], yr[RU];
+#pragma unroll
+        for (int i = 0; i < RU; ++i) {
+            zr[i] = zn;
+            yr[i] = yn;
+            if (++yn == H) {
+                yn = 0;
+                ++zn;
             }
-            dst[k] = p;
         }
-        if (++yy == H) {
-            yy = 0;
-            ++zz;
+        for (int k = tid; k < W; k += nthr) {
+            uint32_t p[RU];
+#pragma unroll
+            for (int i = 0; i < RU; ++i) p[i] = row0 + rl0 + i < nrows ? P[(row0 + rl0 + i) * W + k] : PNONE;
+#pragma unroll
+            for (int i = 0; i < RU; ++i) {
+                if (row0 + rl0 + i < nrows) {
+                    const int dz = zr[i] - (int)(p[i] >> 16), dy = yr[i] - (int)(p[i] & 0xFFFFu);
+                    dmax = max(dmax, p[i] == PNONE ? 32767 : max(abs(dz), abs(dy)));
+                }
+                rec[(rl0 + i) * pitch + k] = p[i];
+            }
         }
     }
     dmax = (int)__reduce_max_sync(FULL, (unsigned)dmax);
@@ -295,7 +345,11 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
             // the warp's own row, rewritten in place: bits 31..24 and 23..16
             // the z and y offsets of the record (each within +-64 here), bits
             // 15..0 their squared length (at most 2 * 64^2), so that a
-            // candidate costs one load and a mask
+            // candidate costs one load and a mask.  The search takes two
+            // steps per test of the stop rule (a step past the stop costs at
+            // least its r^2, more than the best, and changes nothing); the
+            // best is at most 2 * 64^2, so it stops by r = 91 < XPAD and every
+            // look past the row's ends reads a pad.
             for (int k = lane; k < W; k += 32) {
                 const uint32_t p = rr[k];
                 const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
@@ -306,21 +360,15 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
                 const int j = c0 + lane;
                 if (j >= W) continue;
                 int best = (int)(rr[j] & 0xFFFFu), bk = j;
-                for (int r = 1, r2 = 1; r2 <= best; ++r, r2 += 2 * r - 1) {
-                    if (j - r >= 0) {
-                        const int c = (int)(rr[j - r] & 0xFFFFu) + r2;
-                        if (c < best) {
-                            best = c;
-                            bk = j - r;
-                        }
-                    }
-                    if (j + r < W) {
-                        const int c = (int)(rr[j + r] & 0xFFFFu) + r2;
-                        if (c <= best) {
-                            best = c;
-                            bk = j + r;
-                        }
-                    }
+                for (int r = 1, r2 = 1; r2 <= best; r += 2, r2 += 4 * r - 4) {
+                    const int r2b = r2 + 2 * r + 1;
+                    const int cl = (int)(rr[j - r] & 0xFFFFu) + r2, cr = (int)(rr[j + r] & 0xFFFFu) + r2;
+                    const int cl2 = (int)(rr[j - r - 1] & 0xFFFFu) + r2b;
+                    const int cr2 = (int)(rr[j + r + 1] & 0xFFFFu) + r2b;
+                    if (cl < best) { best = cl; bk = j - r; }
+                    if (cr <= best) { best = cr; bk = j + r; }
+                    if (cl2 < best) { best = cl2; bk = j - r - 1; }
+                    if (cr2 <= best) { best = cr2; bk = j + r + 1; }
                 }
                 const uint32_t p = rr[bk];
                 const int dz = (int)(int8_t)(p >> 24), dy = (int)(int8_t)((p >> 16) & 0xFFu);

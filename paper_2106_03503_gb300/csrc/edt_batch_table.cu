@@ -45,12 +45,12 @@ int batch_kind(const edt_job& j, const char** why)
         int lg, NW;
         batch_line_geometry(H, pos, lg, NW);
         if (batch_ypass_group_bytes(H, lg, NW) > BATCH_3D_SMEM) {
-            if (why) *why = "3-D height too large for the batched y pass (about 1536 at most)";
+            if (why) *why = "3-D height too large for the batched y pass (about 1150 at most)";
             return -1;
         }
         batch_line_geometry(W, pos, lg, NW);
         if (batch_xpass_group_bytes(W, lg, NW) > BATCH_3D_SMEM) {
-            if (why) *why = "3-D row width too large for the batched x pass (about 780 at most)";
+            if (why) *why = "3-D row width too large for the batched x pass (about 710 at most)";
             return -1;
         }
     }

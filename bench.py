@@ -363,7 +363,7 @@ def measure_volume(edt, torch, dev, reps=10):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
-    kern = {k: edt.trace_read(k)[0] / reps for k in ("k_colbits", "k_ypass3d", "k_xpass3d")}
+    kern = {k: edt.trace_read(k)[0] / reps for k in ("k_colbits", "k_zoffsets", "k_ypass3d", "k_xpass3d")}
     edt.trace_enable(False)
     n = m.numel()
     import oracle

@@ -37,7 +37,10 @@
  *     sum of (side - 1)^2, must stay below 2^31 - 1 so that D fits int32.
  *   - Scratch memory: the plain calls draw their scratch from the device's
  *     stream-ordered memory pool (cudaMallocAsync on the given stream, freed on
- *     the same stream); batch plans and servers own theirs.
+ *     the same stream): about 0.26 byte per pixel for 2-D images, 2.26 bytes
+ *     per voxel for 3-D volumes (the column pass's words plus every voxel's
+ *     int16 offset to its nearest source along z); batch plans and servers own
+ *     theirs.
  *   - Threads: the plain, pair, host-buffer, city-block and chamfer calls may
  *     be made from several host threads at once (on separate streams, with
  *     separate buffers); a plan is used from one thread at a time and

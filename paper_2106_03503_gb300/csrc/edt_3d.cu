@@ -99,12 +99,74 @@ __host__ __device__ static inline size_t ypass_smem(int H, int lg, int NW)
 
 size_t batch_ypass_group_bytes(int H, int lg, int NW) { return ypass_smem(H, lg, NW); }
 
+// z offsets of the nearest source along z of every voxel, written once for
+// the y pass: d16[z][y][x] = z' - z (int16; YNONE when the column has no
+// source).  A thread takes one column of one band of 32 planes: its word and
+// band summary are read once, then the distances to the nearest source at or
+// below each plane (dd, a backward sweep over the word's bits) and at or
+// above it (du, a forward sweep) follow one step each, the nearer taken as
+// the column pass takes it (the one above at a tie).  A y tile staged from
+// the words would read and decode them once per plane.
+__global__ void __launch_bounds__(256)
+k_zoffsets(int Dz, int64_t cols, ColScratch s, short* __restrict__ d16)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int zb = blockIdx.y;
+    if (p >= cols) return;
+    constexpr int BIG = 60000;   // beyond any distance (< 32768) even after 32 steps
+    const uint32_t w = __ldg(s.C + (int64_t)zb * cols + p);
+    const uint32_t u = __ldg(s.U + (int64_t)zb * cols + p);
+    uint32_t up = u & 0xFFFFu, dn = u >> 16;
+    if (up == (uint32_t)NONE16 || dn == (uint32_t)NONE16) {
+        const uint32_t gab = __ldg(s.GAB + (int64_t)(zb >> s.gs) * cols + p);
+        if (up == (uint32_t)NONE16) up = gab & 0xFFFFu;
+        if (dn == (uint32_t)NONE16) dn = gab >> 16;
+    }
+    const int base = 32 * zb;
+    const int rows = min(32, Dz - base);
+    short* out = d16 + (int64_t)base * cols + p;
+    if (w == 0u && up == (uint32_t)NONE16 && dn == (uint32_t)NONE16) {   // no source in the whole column
+        for (int r = 0; r < rows; ++r) out[(int64_t)r * cols] = YNONE;
+        return;
+    }
+    // with a source somewhere in the column, every plane has one above or
+    // below it, closer than BIG
+    int dd[32];
+    int t = dn == (uint32_t)NONE16 ? BIG : (int)dn - (base + 32);
+#pragma unroll
+    for (int r = 31; r >= 0; --r) {
+        t = (w & (1u << r)) ? 0 : t + 1;
+        dd[r] = t;
+    }
+    int nu = up == (uint32_t)NONE16 ? -BIG : (int)up - (base - 1);   // minus the distance above
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        nu = (w & (1u << r)) ? 0 : nu - 1;
+        if (r < rows) out[(int64_t)r * cols] = (short)(dd[r] < -nu ? dd[r] : nu);
+    }
+}
+
+// 16-byte copy global -> shared that completes at cp_async_wait_all (the
+// copies of a thread are all in flight together and need no registers)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    const uint32_t da = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(da), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // One y-pass tile: plane z, the 32 columns x0 .. x0+31 (one line per lane),
 // NW warps = y segments.  Run by the nthr threads of one engine (tid = thread
-// within it, warp = warp within it) over the shared memory at `base`.
+// within it, warp = warp within it) over the shared memory at `base`.  The z
+// offsets come from d16 (k_zoffsets) when it is given, else from the column
+// pass's words and summaries.
 template <class Sync>
-__device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, uint32_t* __restrict__ P,
-                           int z, int x0, unsigned char* base, int tid, int nthr, int warp, Sync sync)
+__device__ void ypass_tile(int H, int W, const ColScratch& s, const short* __restrict__ d16, int lg, int NW,
+                           uint32_t* __restrict__ P, int z, int x0, unsigned char* base, int tid, int nthr, int warp,
+                           Sync sync)
 {
     short* gz = reinterpret_cast<short*>(base) + YPAD * YP;     // row 0 of the tile
     int* wmax = reinterpret_cast<int*>(base + ytile_bytes(H));
@@ -127,7 +189,44 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, ui
     const int total = H * 32;
     constexpr int SU = 4;
     int dmax = 0;
-    for (int e0 = tid; e0 < total; e0 += SU * nthr) {
+    if (d16 && (W & 7) == 0) {
+        // 8 offsets per 16-byte chunk (every row starts 16-byte aligned): all
+        // of a thread's chunks copied asynchronously at once, chunks past the
+        // volume's edge (whole chunks, W being a multiple of 8) set to YNONE;
+        // then the largest |offset| over the in-volume chunks
+        const short* src = d16 + (int64_t)z * plane + x0;
+        const uint32_t none2 = (uint32_t)(uint16_t)YNONE * 0x10001u;
+        for (int e = tid; e < H * 4; e += nthr) {
+            const int y = e >> 2, xq = (e & 3) * 8;
+            if (x0 + xq < W)
+                cp_async16(gz + y * YP + xq, src + (int64_t)y * W + xq);
+            else
+                *reinterpret_cast<uint4*>(gz + y * YP + xq) = make_uint4(none2, none2, none2, none2);
+        }
+        cp_async_wait_all();
+        sync();
+        for (int e = tid; e < H * 4; e += nthr) {
+            const int y = e >> 2, xq = (e & 3) * 8;
+            if (x0 + xq >= W) continue;
+            const uint4 v = *reinterpret_cast<const uint4*>(gz + y * YP + xq);
+            const uint32_t m = __vmaxs2(__vmaxs2(__vabsss2(v.x), __vabsss2(v.y)),
+                                        __vmaxs2(__vabsss2(v.z), __vabsss2(v.w)));
+            dmax = max(dmax, (int)max(m & 0xFFFFu, m >> 16));
+        }
+    } else if (d16) {
+        // W not a multiple of 8: offset by offset
+        const short* src = d16 + (int64_t)z * plane + x0;
+        for (int e = tid; e < total; e += nthr) {
+            const int y = e >> 5, xl = e & 31;
+            int d = YNONE;
+            if (x0 + xl < W) {
+                d = src[(int64_t)y * W + xl];
+                dmax = max(dmax, abs(d));
+            }
+            gz[y * YP + xl] = (short)d;
+        }
+    }
+    for (int e0 = d16 ? total : tid; e0 < total; e0 += SU * nthr) {
         uint32_t w[SU], u[SU];
 #pragma unroll
         for (int i = 0; i < SU; ++i) {
@@ -204,53 +303,80 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, int lg, int NW, ui
 
 // One block: one z, 32 consecutive x (one line per lane), warps = y segments.
 __global__ void __launch_bounds__(1024)
-k_ypass3d(int H, int W, ColScratch s, int lg, int NW, uint32_t* __restrict__ P)
+k_ypass3d(int H, int W, ColScratch s, const short* __restrict__ d16, int lg, int NW, uint32_t* __restrict__ P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int xtiles = (W + 31) / 32;
     const int z = blockIdx.x / xtiles;
     const int x0 = (blockIdx.x % xtiles) * 32;
-    ypass_tile(H, W, s, lg, NW, P, z, x0, smem, threadIdx.x, blockDim.x, threadIdx.x >> 5, BlockSync());
+    ypass_tile(H, W, s, d16, lg, NW, P, z, x0, smem, threadIdx.x, blockDim.x, threadIdx.x >> 5, BlockSync());
 }
 
 // --- x pass ----------------------------------------------------------------
 
+// x-unit record of a voxel (z, y, x) whose y-pass source is (z', y', x):
+// with dz = z - z' and dy = y - y' both within +-127, bits 31..24 dz, 23..16
+// dy (two's complement), 14..0 dz^2 + dy^2 (at most 2 * 127^2 < 2^15) and bit
+// 15 clear, so that a direct search reads a candidate's squared length with
+// one load and a mask; otherwise bit 15 set, z' in bits 31..16 and y' (< 2048)
+// in bits 14..0; PNONE when the plane has no source.  The voxel's own
+// position (dz = dy = 0) is record 0.
+__device__ __forceinline__ uint32_t xrec_encode(uint32_t p, int z, int y)
+{
+    if (p == PNONE) return PNONE;
+    const int dz = z - (int)(p >> 16), dy = y - (int)(p & 0xFFFFu);
+    if (abs(dz) <= 127 && abs(dy) <= 127)
+        return ((uint32_t)(dz & 0xFF) << 24) | ((uint32_t)(dy & 0xFF) << 16) | (uint32_t)(dz * dz + dy * dy);
+    return (p & 0xFFFF0000u) | 0x8000u | (p & 0x7FFFu);
+}
+// the source (z', y') of a record that is not PNONE
+__device__ __forceinline__ void xrec_source(uint32_t q, int z, int y, int& zs, int& ys)
+{
+    if (q & 0x8000u) {
+        zs = (int)(q >> 16);
+        ys = (int)(q & 0x7FFFu);
+    } else {
+        zs = z - (int)(int8_t)(q >> 24);
+        ys = y - (int)(int8_t)((q >> 16) & 0xFFu);
+    }
+}
+
 struct LineX {
-    const uint32_t* rec;     // this lane's row of (z', y') records (pitch odd)
+    const uint32_t* rec;     // this lane's row of records (xrec_encode)
     int z, y, H, W;
-    uint32_t self;           // this row's own record, (z << 16) | y
     bool valid;
+    __device__ __forceinline__ int sq(uint32_t q) const
+    {
+        if (!(q & 0x8000u)) return (int)(q & 0x7FFFu);
+        const int dz = z - (int)(q >> 16), dy = y - (int)(q & 0x7FFFu);
+        return dz * dz + dy * dy;
+    }
     __device__ __forceinline__ bool eval(int k, int& f) const
     {
         if (!valid) return false;
-        const uint32_t p = rec[k];
-        if (p == PNONE) return false;
-        const int dz = z - (int)(p >> 16), dy = y - (int)(p & 0xFFFFu);
-        f = dz * dz + dy * dy;
+        const uint32_t q = rec[k];
+        if (q == PNONE) return false;
+        f = sq(q);
         return true;
     }
-    __device__ __forceinline__ int c(int k) const
-    {
-        const uint32_t p = rec[k];
-        const int dz = z - (int)(p >> 16), dy = y - (int)(p & 0xFFFFu);
-        return dz * dz + dy * dy + k * k;
-    }
+    __device__ __forceinline__ int c(int k) const { return sq(rec[k]) + k * k; }
     __device__ __forceinline__ bool eval2(int k, int& f, int& feat) const
     {
         if (!valid) return false;
-        const uint32_t p = rec[k];
-        if (p == PNONE) return false;
-        const int zz = (int)(p >> 16), yy = (int)(p & 0xFFFFu);
-        f = (z - zz) * (z - zz) + (y - yy) * (y - yy);
-        feat = (zz * H + yy) * W + k;
+        const uint32_t q = rec[k];
+        if (q == PNONE) return false;
+        int zs, ys;
+        xrec_source(q, z, y, zs, ys);
+        f = sq(q);
+        feat = (zs * H + ys) * W + k;
         return true;
     }
-    __device__ __forceinline__ bool is_zero(int k) const { return rec[k] == self; }
+    __device__ __forceinline__ bool is_zero(int k) const { return rec[k] == 0u; }
     __device__ __forceinline__ bool chunk_has_source(int j0) const
     {
         bool any = false;
 #pragma unroll
-        for (int t = 0; t < OC; ++t) any |= rec[j0 + t] == self;
+        for (int t = 0; t < OC; ++t) any |= rec[j0 + t] == 0u;
         return any;
     }
     __device__ __forceinline__ int self_feature(int k) const { return (z * H + y) * W + k; }
@@ -318,11 +444,13 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
             for (int i = 0; i < RU; ++i) p[i] = row0 + rl0 + i < nrows ? P[(row0 + rl0 + i) * W + k] : PNONE;
 #pragma unroll
             for (int i = 0; i < RU; ++i) {
+                uint32_t q = PNONE;
                 if (row0 + rl0 + i < nrows) {
                     const int dz = zr[i] - (int)(p[i] >> 16), dy = yr[i] - (int)(p[i] & 0xFFFFu);
                     dmax = max(dmax, p[i] == PNONE ? 32767 : max(abs(dz), abs(dy)));
+                    q = xrec_encode(p[i], zr[i], yr[i]);
                 }
-                rec[(rl0 + i) * pitch + k] = p[i];
+                rec[(rl0 + i) * pitch + k] = q;
             }
         }
     }
@@ -341,21 +469,13 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
             const int64_t row = row0 + rl;
             if (row >= nrows) break;
             const int zz = (int)(row / H), yy = (int)(row % H);
-            uint32_t* rr = rec + rl * pitch;
-            // the warp's own row, rewritten in place: bits 31..24 and 23..16
-            // the z and y offsets of the record (each within +-64 here), bits
-            // 15..0 their squared length (at most 2 * 64^2), so that a
-            // candidate costs one load and a mask.  The search takes two
-            // steps per test of the stop rule (a step past the stop costs at
-            // least its r^2, more than the best, and changes nothing); the
+            const uint32_t* rr = rec + rl * pitch;
+            // every record of this unit has its offsets within +-64, so bits
+            // 15..0 are its squared length (xrec_encode).  The search takes
+            // two steps per test of the stop rule (a step past the stop costs
+            // at least its r^2, more than the best, and changes nothing); the
             // best is at most 2 * 64^2, so it stops by r = 91 < XPAD and every
             // look past the row's ends reads a pad.
-            for (int k = lane; k < W; k += 32) {
-                const uint32_t p = rr[k];
-                const int dz = zz - (int)(p >> 16), dy = yy - (int)(p & 0xFFFFu);
-                rr[k] = ((uint32_t)(dz & 0xFF) << 24) | ((uint32_t)(dy & 0xFF) << 16) | (uint32_t)(dz * dz + dy * dy);
-            }
-            __syncwarp();
             for (int c0 = 0; c0 < W; c0 += 32) {
                 const int j = c0 + lane;
                 if (j >= W) continue;
@@ -389,7 +509,6 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
     line.H = H;
     line.W = W;
     line.valid = row < nrows;
-    line.self = ((uint32_t)line.z << 16) | (uint32_t)line.y;
     const int vec = row_vec_width(W, D, F, dist);
     const RowOut out{D, F, dist, row * W, row < nrows, vec};
     band_envelope(line, out, sm, W, lg, NW, nullptr, warp, sync);
@@ -448,7 +567,7 @@ k_batch_ypass3d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
         const int64_t unit = (item - J.k_first[PH_Y]) * J.groups + grp;
         if (grp < J.groups && unit < (int64_t)J.Dz * xtiles) {
             unsigned char* base = smem + (size_t)grp * ypass_smem(J.H, J.lg, NW);
-            ypass_tile(J.H, J.W, J.s, J.lg, NW, reinterpret_cast<uint32_t*>(J.F), (int)(unit / xtiles),
+            ypass_tile(J.H, J.W, J.s, nullptr, J.lg, NW, reinterpret_cast<uint32_t*>(J.F), (int)(unit / xtiles),
                        (int)(unit % xtiles) * 32, base, wg * 32 + lane, NW * 32, wg, GroupSync{1 + grp, NW * 32});
         }
         __syncthreads();
@@ -534,8 +653,17 @@ static void pick_band(int n, size_t (*smem_fn)(int, int, int), int max_nw, int& 
     }
 }
 
+cudaError_t launch_zoffsets(int Dz, int H, int W, const ColGeom& g, const ColScratch& s, short* d16,
+                            cudaStream_t stream)
+{
+    const int64_t cols = (int64_t)H * W;
+    const dim3 grid((unsigned)((cols + 255) / 256), (unsigned)g.nb);
+    k_zoffsets<<<grid, 256, 0, stream>>>(Dz, cols, s, d16);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
-                           const ColScratch& s, uint32_t* P, cudaStream_t stream)
+                           const ColScratch& s, const short* d16, uint32_t* P, cudaStream_t stream)
 {
     (void)g;
     // 8 warps: the y pass's shared memory is small (32 lines of 2-byte
@@ -547,7 +675,7 @@ cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
     pick_band(H, ypass_smem, tu.ypass_nw > 0 ? tu.ypass_nw : 8, lg, NW);
     const int xtiles = (W + 31) / 32;
     const unsigned blocks = (unsigned)((int64_t)Dz * xtiles);
-    k_ypass3d<<<blocks, NW * 32, ypass_smem(H, lg, NW), stream>>>(H, W, s, lg, NW, P);
+    k_ypass3d<<<blocks, NW * 32, ypass_smem(H, lg, NW), stream>>>(H, W, s, d16, lg, NW, P);
     return cudaGetLastError();
 }
 

@@ -119,9 +119,10 @@ edt_status check_shape(int ndim, const int* shape, int mode)
 // Bytes of device scratch one transform needs.
 size_t scratch_bytes(int ndim, const int* shape)
 {
-    const ColGeom g = (ndim == 2) ? col_geom(shape[0], shape[1])
-                                  : col_geom(shape[0], (int64_t)shape[1] * shape[2]);
-    return col_scratch_bytes(g);
+    if (ndim == 2) return col_scratch_bytes(col_geom(shape[0], shape[1]));
+    // 3-D: the z pass's scratch, then the int16 z offsets of every voxel
+    const ColGeom g = col_geom(shape[0], (int64_t)shape[1] * shape[2]);
+    return ((col_scratch_bytes(g) + 255) & ~size_t(255)) + (size_t)shape[0] * shape[1] * shape[2] * 2;
 }
 
 // Enqueue one transform using `scratch` (scratch_bytes() bytes, device).
@@ -146,12 +147,17 @@ edt_status run_transform(const uint8_t* mask, int ndim, const int* shape, int mo
     const int Dz = shape[0], H = shape[1], W = shape[2];
     const ColGeom g = col_geom(Dz, (int64_t)H * W);
     const ColScratch s = col_scratch_carve(scratch, g);
+    short* d16 = reinterpret_cast<short*>(static_cast<char*>(scratch) + ((col_scratch_bytes(g) + 255) & ~size_t(255)));
     uint32_t* P = reinterpret_cast<uint32_t*>(F ? F : D);
     if ((e = cudaMemsetAsync(s.cnt, 0, (size_t)g.ntiles * 4, stream)) != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync");
     if ((e = traced("k_colbits", stream, [&] { return launch_colbits(mask, g, mode, s, stream); })) != cudaSuccess)
         return cuda_fail(e, "z pass launch");
-    if ((e = traced("k_ypass3d", stream, [&] { return launch_ypass3d(Dz, H, W, g, s, P, stream); })) != cudaSuccess)
+    if ((e = traced("k_zoffsets", stream, [&] { return launch_zoffsets(Dz, H, W, g, s, d16, stream); })) !=
+        cudaSuccess)
+        return cuda_fail(e, "z offsets launch");
+    if ((e = traced("k_ypass3d", stream, [&] { return launch_ypass3d(Dz, H, W, g, s, d16, P, stream); })) !=
+        cudaSuccess)
         return cuda_fail(e, "y pass launch");
     if ((e = traced("k_xpass3d", stream,
                     [&] { return launch_xpass3d(Dz, H, W, P, D, F, dist, stream); })) != cudaSuccess)

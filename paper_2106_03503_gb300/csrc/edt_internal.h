@@ -72,8 +72,13 @@ cudaError_t launch_colbits_sheared(const uint8_t* mask, const ColGeom& g, int mo
 size_t chamfer_scratch_bytes(int H, int W);
 cudaError_t launch_chamfer(const uint8_t* mask, int H, int W, int mode, int32_t* D, void* scratch,
                            int sm_count, cudaStream_t stream);
+// 3-D: the z offset of every voxel's nearest source along z (int16,
+// Dz*H*W entries) from the z column pass's scratch, then the y pass over
+// them (d16 NULL: the y pass decodes the column words itself) and the x pass.
+cudaError_t launch_zoffsets(int Dz, int H, int W, const ColGeom& g, const ColScratch& s, short* d16,
+                            cudaStream_t stream);
 cudaError_t launch_ypass3d(int Dz, int H, int W, const ColGeom& g,
-                           const ColScratch& s, uint32_t* P, cudaStream_t stream);
+                           const ColScratch& s, const short* d16, uint32_t* P, cudaStream_t stream);
 cudaError_t launch_xpass3d(int Dz, int H, int W, uint32_t* P, int32_t* D,
                            int32_t* F, float* dist, cudaStream_t stream);
 

@@ -120,8 +120,10 @@ static int run3d(int Dz, int H, int W, double p, int mode)
     int32_t* D = alloc_words(n);
     int32_t* F = alloc_words(n);
     float* dist = reinterpret_cast<float*>(alloc_words(n));
+    short* d16 = reinterpret_cast<short*>(alloc_words((n + 1) / 2));   // the z offsets, as run_transform carves them
     launch_colbits(mask.data(), g, mode, s, nullptr);
-    launch_ypass3d(Dz, H, W, g, s, reinterpret_cast<uint32_t*>(F), nullptr);
+    launch_zoffsets(Dz, H, W, g, s, d16, nullptr);
+    launch_ypass3d(Dz, H, W, g, s, d16, reinterpret_cast<uint32_t*>(F), nullptr);
     launch_xpass3d(Dz, H, W, reinterpret_cast<uint32_t*>(F), D, F, dist, nullptr);
     std::vector<int32_t> Do(n), Fo(n);
     oracle_edt3d(mask.data(), Dz, H, W, mode, Do.data(), Fo.data());
@@ -129,7 +131,7 @@ static int run3d(int Dz, int H, int W, double p, int mode)
     int bad = 0;
     for (size_t q = 0; q < n && bad < 5; ++q)
         if (D[q] != Do[q]) { fprintf(stderr, "3-D D mismatch %dx%dx%d at %zu: %d vs %d\n", Dz, H, W, q, D[q], Do[q]); ++bad; }
-    free(D); free(F); free(dist);
+    free(D); free(F); free(dist); free(d16);
     return bad;
 }
 

@@ -21,6 +21,9 @@ for name in ["edt_engine.cuh", "edt_internal.h", "edt_colpass.cu", "edt_rows2d.c
                'emu_tma_store(m, buf, x, row0);', s, flags=re.S)
     s = re.sub(r'asm volatile\("(cp\.async\.bulk\.wait_group[^"]*|fence\.proxy[^"]*|cp\.async\.bulk\.commit_group;)" ::: "memory"\);', ';', s)
     s = re.sub(r'asm volatile\("bar\.sync %0, %1;" ::"r"\(id\), "r"\(nthreads\) : "memory"\);', 'emu_bar_sync(id, nthreads);', s)
+    s = re.sub(r'const uint32_t da = \(uint32_t\)__cvta_generic_to_shared\(dst\);\s*asm volatile\("cp\.async\.cg\.shared\.global.*?: "memory"\);',
+               'memcpy(dst, src, 16);', s, flags=re.S)
+    s = re.sub(r'asm volatile\("cp\.async\.commit_group;\\n\\tcp\.async\.wait_group 0;" ::: "memory"\);', ';', s)
     # launches
     def split_top(t):
         parts, depth, cur = [], 0, ""

@@ -42,6 +42,26 @@ inline uint2 make_uint2(unsigned a, unsigned b) { return {a, b}; }
 struct float4 { float x, y, z, w; };
 inline int4 make_int4(int a, int b, int c, int d) { return {a, b, c, d}; }
 inline float4 make_float4(float a, float b, float c, float d) { return {a, b, c, d}; }
+inline uint4 make_uint4(unsigned a, unsigned b, unsigned c, unsigned d) { return {a, b, c, d}; }
+// per-halfword signed |x| (saturated) and signed maximum
+inline unsigned __vabsss2(unsigned a)
+{
+    unsigned r = 0;
+    for (int i = 0; i < 2; ++i) {
+        const int h = (int16_t)(a >> (16 * i));
+        r |= (unsigned)(uint16_t)(h == -32768 ? 32767 : (h < 0 ? -h : h)) << (16 * i);
+    }
+    return r;
+}
+inline unsigned __vmaxs2(unsigned a, unsigned b)
+{
+    unsigned r = 0;
+    for (int i = 0; i < 2; ++i) {
+        const int x = (int16_t)(a >> (16 * i)), y = (int16_t)(b >> (16 * i));
+        r |= (unsigned)(uint16_t)(x > y ? x : y) << (16 * i);
+    }
+    return r;
+}
 
 inline int __clz(uint32_t x) { return x ? __builtin_clz(x) : 32; }
 inline int __ffs(uint32_t x) { return x ? __builtin_ctz(x) + 1 : 0; }

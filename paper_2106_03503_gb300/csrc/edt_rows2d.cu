@@ -88,15 +88,23 @@ __host__ __device__ inline size_t band2d_col_bytes(int W)
     return (((size_t)8 * W + (size_t)(W + 31) / 32 + 15) & ~size_t(15));
 }
 // Direct row pass (rows2d_direct): rows up to DIRECT_ROW_W wide, one row's
-// vertical offsets per warp in shared memory, searches give up after
-// DIRECT_ROW_CAP columns.
+// vertical offsets per warp in shared memory with DPAD entries of pad on both
+// sides, searches give up after DIRECT_ROW_CAP columns.  OFF_NONE marks a
+// column (or pad) without source: its cost 32767^2 exceeds that of any real
+// candidate (offsets are at most 32766, searches at most DPAD long).
 constexpr int DIRECT_ROW_W = 1024;
-constexpr int DIRECT_ROW_CAP = 64;
-constexpr short OFF_NONE = -32768;
+constexpr int DIRECT_ROW_CAP = 32;
+constexpr int DPAD = DIRECT_ROW_CAP + 2;
+constexpr short OFF_NONE = 32767;
 
 __host__ __device__ inline size_t direct_row_bytes(int W, int NW)
 {
-    return W <= DIRECT_ROW_W ? (((size_t)NW * W * 2 + 15) & ~size_t(15)) : 0;
+    return W <= DIRECT_ROW_W ? (((size_t)NW * (W + 2 * DPAD) * 2 + 15) & ~size_t(15)) : 0;
+}
+// this warp's row of offsets (entry 0 = column 0; pads before and after)
+__device__ __forceinline__ short* direct_rowbuf(void* base, int warp, int W)
+{
+    return reinterpret_cast<short*>(base) + (size_t)warp * (W + 2 * DPAD) + DPAD;
 }
 
 static size_t band2d_smem(int W, int lg, int NW)
@@ -158,6 +166,10 @@ __device__ bool rows2d_direct(const uint32_t* sbits, const uint32_t* supdn, int 
                               int NW, Sync sync, int rlo = 0, int rhi = 32)
 {
     const int base = b * 32, rows = min(rhi, H - base);
+    for (int t = lane; t < DPAD; t += 32) {   // the pads: no source beyond the row's ends
+        rowbuf[-1 - t] = OFF_NONE;
+        rowbuf[W + t] = OFF_NONE;
+    }
     for (int r = rlo + warp; r < rows; r += NW) {
         if (*abort) break;
         const int i = base + r;
@@ -176,35 +188,32 @@ __device__ bool rows2d_direct(const uint32_t* sbits, const uint32_t* supdn, int 
             const int j = c0 + lane;
             bool unsettled = false;
             if (j < W) {
-                int best = INT32_MAX, bk = -1;
+                // two steps per test of the stop rule (a step past the stop
+                // costs at least its r^2, more than the best, and changes
+                // nothing); the pads make bounds tests unneeded
                 const int o = rowbuf[j];
-                if (o != OFF_NONE) {
-                    best = o * o;
-                    bk = j;
-                }
+                int best = o * o, bk = j;
                 int rr = 1;
-                for (; rr <= DIRECT_ROW_CAP && rr * rr <= best; ++rr) {
-                    if (j - rr >= 0) {
-                        const int ol = rowbuf[j - rr];
-                        if (ol != OFF_NONE && ol * ol + rr * rr < best) {
-                            best = ol * ol + rr * rr;
-                            bk = j - rr;
-                        }
-                    }
-                    if (j + rr < W) {
-                        const int orr = rowbuf[j + rr];
-                        if (orr != OFF_NONE && orr * orr + rr * rr <= best) {
-                            best = orr * orr + rr * rr;
-                            bk = j + rr;
-                        }
-                    }
+                for (int r2 = 1; rr <= DIRECT_ROW_CAP && r2 <= best; rr += 2, r2 += 4 * rr - 4) {
+                    const int r2b = r2 + 2 * rr + 1;
+                    const int ol = rowbuf[j - rr], orr = rowbuf[j + rr];
+                    const int ol2 = rowbuf[j - rr - 1], orr2 = rowbuf[j + rr + 1];
+                    const int cl = ol * ol + r2, cr = orr * orr + r2;
+                    const int cl2 = ol2 * ol2 + r2b, cr2 = orr2 * orr2 + r2b;
+                    if (cl < best) { best = cl; bk = j - rr; }
+                    if (cr <= best) { best = cr; bk = j + rr; }
+                    if (cl2 < best) { best = cl2; bk = j - rr - 1; }
+                    if (cr2 <= best) { best = cr2; bk = j + rr + 1; }
                 }
+                // rr: the nearest distance not searched
                 unsettled = rr * rr <= best && (j - rr >= 0 || j + rr < W);
                 if (!unsettled) {
+                    const int ob = rowbuf[bk];
+                    const bool none = ob == OFF_NONE;   // the whole row has no source
                     const int64_t q = (int64_t)i * W + j;
-                    const int v = bk < 0 ? INT32_MAX : best;
+                    const int v = none ? INT32_MAX : best;
                     if (D) D[q] = v;
-                    if (F) F[q] = bk < 0 ? -1 : (i + rowbuf[bk]) * W + bk;
+                    if (F) F[q] = none ? -1 : (i + ob) * W + bk;
                     if (dist) dist[q] = sqrt_rn_int(v);
                 }
             }
@@ -308,7 +317,7 @@ k_rows2d(int H, int W, int band0, int nbl, RowJob J0, RowJob J1, int lg, int NW,
         stage_band(J.s, b, H, W, sbits, supdn, sfull, threadIdx.x, blockDim.x, J.invert != 0);
         __syncthreads();
         // narrow rows: the direct search, unless some pixel's answer is far
-        short* rowbuf = reinterpret_cast<short*>(reinterpret_cast<unsigned char*>(sm.ctr) + 16) + warp * W;
+        short* rowbuf = direct_rowbuf(reinterpret_cast<unsigned char*>(sm.ctr) + 16, warp, W);
         if (rows2d_direct(sbits, supdn, b, H, W, J.D, J.F, J.dist, rowbuf, &s_abort, lane, warp, NW, BlockSync(),
                           rlo, rhi))
             return;
@@ -501,7 +510,7 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
             sync();
             bool done = false;
             if (W <= DIRECT_ROW_W) {
-                short* rowbuf = reinterpret_cast<short*>(reinterpret_cast<unsigned char*>(sm.ctr) + 16) + wg * W;
+                short* rowbuf = direct_rowbuf(reinterpret_cast<unsigned char*>(sm.ctr) + 16, wg, W);
                 done = rows2d_direct(sbits, supdn, b, H, W, J.D, J.F, J.dist, rowbuf, &s_abort[grp], lane, wg, NW,
                                      sync);
             }

@@ -393,7 +393,7 @@ cudaError_t launch_colbits_sheared(const uint8_t* mask, const ColGeom& g, int mo
 
 // Persistent column pass over every job of a batch (for a 3-D job the z pass
 // over its Dz x H*W view): warp units are numbered job by job
-// (k_first[PH_COL]); every warp takes one contiguous range of them, so that it
+// (k_first[PH_COL]); warp w takes units w, w + (warps of the grid), ...: it
 // finds its first job by binary search once and then steps from job to job.
 __global__ void __launch_bounds__(K1_WARPS * 32)
 k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs)
@@ -403,17 +403,19 @@ k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
     const int warp = threadIdx.x >> 5;
     const int64_t total = hdr->k_total[PH_COL];
     const int nj = hdr->njobs;
+    // units round-robin over the grid's warps: neighbouring tiles of a group
+    // (whose rows share the 32-byte sectors their windows straddle) are read
+    // at about the same time, so a shared sector comes from DRAM once
     const int64_t nw = (int64_t)gridDim.x * K1_WARPS, w = (int64_t)blockIdx.x * K1_WARPS + warp;
-    const int64_t g0 = total * w / nw, g1 = total * (w + 1) / nw;
     int lo = 0;
-    if (g0 < g1) {
+    if (w < total) {
         int hi = nj - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].k_first[PH_COL] <= g0) lo = mid; else hi = mid - 1;
+            if (jobs[mid].k_first[PH_COL] <= w) lo = mid; else hi = mid - 1;
         }
     }
-    for (int64_t gw = g0; gw < g1; ++gw) {
+    for (int64_t gw = w; gw < total; gw += nw) {
         while (lo + 1 < nj && jobs[lo + 1].k_first[PH_COL] <= gw) ++lo;
         const BatchJob& J = jobs[lo];
         const ColGeom g = J.g;

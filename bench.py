@@ -508,8 +508,9 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
     side 64..256 of smoothed noise), D+F, host buffers, 40 GB budget.
 
     Each job takes one of `pool_size` distinct masks drawn from that recipe
-    beforehand (untimed, pinned).  A burst of `warm` jobs (after 30 untimed
-    ones) measures the capacity in pixels per second; `n_jobs` jobs then
+    beforehand (untimed, pinned).  After an untimed burst of `warm` jobs
+    (which also pins the client's result buffers), a second burst of `warm`
+    jobs measures the capacity in pixels per second; `n_jobs` jobs then
     arrive as a Poisson stream at that capacity (load 1.0: the throughput the
     server sustains), and again at each lower load x the sustained rate.  A
     job's latency runs from its scheduled arrival to the server's completion
@@ -526,22 +527,35 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
     specs = inputs.serving_jobs(pool_size, seed)
     with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
         pool = [torch.from_numpy(m).pin_memory() for m in ex.map(inputs.draw_job, specs)]
-    maxn = max(m.numel() for m in pool)
-    depth = 32
-    ring = [(torch.empty(maxn, dtype=torch.int32).pin_memory(),
-             torch.empty(maxn, dtype=torch.int32).pin_memory()) for _ in range(depth)]
+    # result buffers (pinned) in power-of-two size classes, kept for reuse:
+    # up to `depth` jobs in flight without pinning depth x the largest job
+    depth = 64
+    classes = {}
     srv = edt.Server(40 << 30, n_streams=3)
-    free = list(range(depth))
     busy = {}
+
+    class Slots:
+        def __bool__(self):
+            return len(busy) < depth
+
+    free = Slots()
+
+    def take(n):
+        c = max(14, (n - 1).bit_length())
+        lst = classes.setdefault(c, [])
+        if lst:
+            return c, lst.pop()
+        return c, (torch.empty(1 << c, dtype=torch.int32).pin_memory(),
+                   torch.empty(1 << c, dtype=torch.int32).pin_memory())
 
     def submit(k, t_arrival):
         m = pool[k]
-        slot = free.pop()
-        D = ring[slot][0][:m.numel()].view(m.shape)
-        F = ring[slot][1][:m.numel()].view(m.shape)
+        c, (Db, Fb) = take(m.numel())
+        D = Db[:m.numel()].view(m.shape)
+        F = Fb[:m.numel()].view(m.shape)
         t_sub = time.perf_counter()
         t = srv.submit(m, 0, out=(D, F, None))
-        busy[t] = (slot, m.numel(), t_arrival, t_sub)
+        busy[t] = ((c, (Db, Fb)), m.numel(), t_arrival, t_sub)
         return t
 
     def reap(recs):
@@ -551,8 +565,8 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
         for t in list(busy):
             r = srv.poll_detail(t)
             if r is not None:
-                slot, n, t_arr, t_sub = busy.pop(t)
-                free.append(slot)
+                (c, bufs), n, t_arr, t_sub = busy.pop(t)
+                classes[c].append(bufs)
                 recs.append({"px": n, "late": t_sub - t_arr, "latency": r[0], "wait": r[1]})
                 got = True
         if not got:
@@ -570,11 +584,11 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
                 reap(recs)
         return time.perf_counter() - t0, sum(r["px"] for r in recs)
 
-    burst(rng.integers(0, pool_size, size=30))            # untimed: pools, plans, graphs
-    order = rng.integers(0, pool_size, size=warm + n_jobs)
-    secs, px_burst = burst(order[:warm])                   # warm-up and capacity
+    order = rng.integers(0, pool_size, size=2 * warm + n_jobs)
+    burst(order[:warm])                                    # untimed warm-up: pools, plans, graphs, result buffers
+    secs, px_burst = burst(order[warm:2 * warm])           # capacity
     cap_px = px_burst / secs
-    stream = order[warm:]
+    stream = order[2 * warm:]
     mean_px = float(np.mean([pool[int(k)].numel() for k in stream]))
 
     def poisson_run(rate):
@@ -614,11 +628,12 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
     runs.append(sat)
     srv.close()
     # the plain path on the same job stream: one synchronous host-buffer call per job
+    _, (Db, Fb) = take(max(m.numel() for m in pool))
     t0 = time.perf_counter()
     for k in stream:
         m = pool[int(k)]
-        D = ring[0][0][:m.numel()].view(m.shape)
-        F = ring[0][1][:m.numel()].view(m.shape)
+        D = Db[:m.numel()].view(m.shape)
+        F = Fb[:m.numel()].view(m.shape)
         edt.feature_host(m, 0, D=D, F=F)
     plain_s = time.perf_counter() - t0
     plain_gpx = sum(pool[int(k)].numel() for k in stream) / plain_s / 1e9
@@ -637,7 +652,8 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
             "plain": "the same job stream, one synchronous edt_feature_host call per job",
             "sweep": runs,
             "note": f"{pool_size} distinct masks of the recipe (pinned, drawn untimed), each job one of them; "
-                    f"at most {depth} jobs in flight; latency from the scheduled arrival"}
+                    f"at most {depth} jobs in flight, their pinned result buffers reused in power-of-two size "
+                    f"classes; latency from the scheduled arrival"}
 
 
 def run_reference(args, rank, world):

@@ -201,8 +201,9 @@ edt_status edt_batch_tune_get(int ndim, const int *shape, int *values);
  * mem_budget_bytes, copies them in, groups the admitted jobs into batches
  * (edt_batch's kernels; 3-D volumes beyond the batch limits run as plain
  * transforms), runs them on n_streams streams so that batches overlap, copies
- * results out and completes the ticket once the device has finished, with
- * the device's status (a GPU error after enqueueing fails the ticket).  Each result is identical to a plain edt_feature
+ * results out job by job and completes each ticket once that job's results
+ * are on the host, with the device's status (a GPU error after enqueueing
+ * fails the ticket).  Each result is identical to a plain edt_feature
  * call on the same mask.  The budget is taken from the device when the
  * server is created (a memory pool of its own, grown to the budget less the
  * batch plans' scratch) and given back by edt_serve_destroy; EDT_ERR_BUDGET

@@ -7,11 +7,13 @@
 // the batch's column-pass scratch) from the server's memory pool, and
 // enqueues on that stream: the mask copies in, batched replays for every job
 // the batch kernels cover (2-D of any width, 3-D volumes up to the batch
-// limits) and plain transforms for the rest (larger volumes), the result
-// copies out, the buffer frees, and an event.  A completion thread per stream
-// waits for that event and completes the tickets with the status the device
-// reports (an error raised by the GPU after enqueueing fails the tickets),
-// then returns their bytes to the budget.  Batches on different streams
+// limits) and plain transforms for the rest (larger volumes), each job's
+// result copies out followed by an event of that job, the buffer frees, and
+// a last event.  A completion thread per stream waits for the jobs' events in
+// turn and completes each ticket as soon as its job's results are on the
+// host, with the status the device reports (an error raised by the GPU after
+// enqueueing fails the tickets), returning the job's bytes to the budget; the
+// last event frees the stream.  Batches on different streams
 // overlap on the device; requests that arrive while batches run are admitted
 // as soon as a stream and enough budget are free.  Every result is the same as
 // a plain edt_feature call on the same mask (the kernels do not depend on
@@ -48,8 +50,8 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int SERVE_PLAN_JOBS = 512;          // jobs per batched launch
-// pixels admitted to one stream at a time (beyond the first job): a batch's
-// tickets complete together, so a long backlog is split over the streams in
+// pixels admitted to one stream at a time (beyond the first job): a stream
+// is busy until its whole batch is done, so a long backlog is split over the streams in
 // batches of a few milliseconds of work instead of going to one stream whole
 constexpr int64_t SERVE_BATCH_PIXELS = (int64_t)1 << 25;
 
@@ -70,8 +72,10 @@ struct Ticket {
 };
 
 struct Completion {
-    size_t bytes;
+    size_t bytes;            // budget bytes of the batch not yet given back
     std::vector<uint64_t> tickets;
+    std::vector<size_t> job_bytes;
+    int recorded = 0;        // jobs 0 .. recorded-1 have their own event
     edt_status status;       // of the enqueueing
 };
 
@@ -80,6 +84,7 @@ struct StreamSlot {
     cudaStream_t stream = nullptr;
     edt_plan* plan = nullptr;
     cudaEvent_t done = nullptr;
+    std::vector<cudaEvent_t> job_done;   // one per job of a batch: its results are on the host
     bool busy = false;
     Completion* pending = nullptr;   // enqueued, waiting for `done`
     std::thread completer;
@@ -107,33 +112,51 @@ struct edt_server {
 
 namespace {
 
-// Completion thread of stream slot `si`: waits for each enqueued batch's
-// event, then completes its tickets with the device's status and gives the
-// bytes back to the budget.
+// Completion thread of stream slot `si`: for each enqueued batch, completes
+// every job's ticket as soon as that job's results are on the host (its own
+// event, recorded after its copies back), with the device's status, and gives
+// its bytes back to the budget; then waits for the batch's last event and
+// frees the stream.
 void completer(edt_server* s, int si)
 {
     cudaSetDevice(s->device);
     StreamSlot& slot = s->slots[si];
     std::unique_lock<std::mutex> lk(s->mu);
+    auto finish = [&](uint64_t t, edt_status status, size_t bytes) {   // with the lock held
+        auto it = s->tickets.find(t);
+        if (it != s->tickets.end()) {
+            it->second.state = 2;
+            it->second.status = status;
+            it->second.latency = std::chrono::duration<double>(Clock::now() - it->second.t_submit).count();
+        }
+        s->in_use -= bytes;
+        --s->outstanding;
+    };
     for (;;) {
         s->cv.wait(lk, [&] { return slot.pending != nullptr || (s->stopping && !slot.busy); });
         if (!slot.pending) break;
         Completion* c = slot.pending;
         lk.unlock();
+        size_t given = 0;
+        for (int k = 0; k < c->recorded; ++k) {
+            const cudaError_t e = cudaEventSynchronize(slot.job_done[k]);
+            edt_status status = c->status;
+            if (status == EDT_OK && e != cudaSuccess) status = EDT_ERR_CUDA;
+            lk.lock();
+            finish(c->tickets[k], status, c->job_bytes[k]);
+            given += c->job_bytes[k];
+            s->cv.notify_all();
+            lk.unlock();
+        }
         const cudaError_t e = cudaEventSynchronize(slot.done);
         edt_status status = c->status;
         if (status == EDT_OK && e != cudaSuccess) status = EDT_ERR_CUDA;
-        const auto now = Clock::now();
         lk.lock();
-        for (uint64_t t : c->tickets) {
-            auto it = s->tickets.find(t);
-            if (it == s->tickets.end()) continue;
-            it->second.state = 2;
-            it->second.status = status;
-            it->second.latency = std::chrono::duration<double>(now - it->second.t_submit).count();
+        for (size_t k = (size_t)c->recorded; k < c->tickets.size(); ++k) {
+            finish(c->tickets[k], status, c->job_bytes[k]);
+            given += c->job_bytes[k];
         }
-        s->in_use -= c->bytes;
-        s->outstanding -= (int)c->tickets.size();
+        s->in_use -= c->bytes - given;   // the rest of the batch's bytes (none when every job was counted)
         slot.pending = nullptr;
         slot.busy = false;
         delete c;
@@ -222,6 +245,14 @@ void launch_batch(edt_server* s, int si, std::vector<Pending>& batch, size_t byt
         off += cnt;
     }
     for (void* sc : bscratch) cudaFreeAsync(sc, st);
+    // results back job by job, each followed by its own event, so that a
+    // job's ticket completes when its own results are on the host
+    int recorded = 0;
+    while (slot.job_done.size() < batch.size()) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) break;
+        slot.job_done.push_back(ev);
+    }
     for (size_t k = 0; k < batch.size(); ++k) {
         const Pending& p = batch[k];
         const Dev& d = dev[k];
@@ -233,6 +264,9 @@ void launch_batch(edt_server* s, int si, std::vector<Pending>& batch, size_t byt
             if (e == cudaSuccess && p.job.dist)
                 e = cudaMemcpyAsync(p.job.dist, d.dist, n * 4, cudaMemcpyDeviceToHost, st);
             if (e != cudaSuccess) status = cuda_fail(e, "serve: result copy");
+            if (status == EDT_OK && (size_t)recorded == k && k < slot.job_done.size() &&
+                cudaEventRecord(slot.job_done[k], st) == cudaSuccess)
+                ++recorded;
         }
         if (d.mask) cudaFreeAsync(d.mask, st);
         if (d.D) cudaFreeAsync(d.D, st);
@@ -240,8 +274,11 @@ void launch_batch(edt_server* s, int si, std::vector<Pending>& batch, size_t byt
         if (d.dist) cudaFreeAsync(d.dist, st);
         if (d.scratch) cudaFreeAsync(d.scratch, st);
     }
-    Completion* c = new Completion{bytes, {}, status};
-    for (const Pending& p : batch) c->tickets.push_back(p.ticket);
+    Completion* c = new Completion{bytes, {}, {}, status == EDT_OK ? recorded : 0, status};
+    for (const Pending& p : batch) {
+        c->tickets.push_back(p.ticket);
+        c->job_bytes.push_back(p.bytes);
+    }
     cudaError_t e = cudaEventRecord(slot.done, st);
     if (e != cudaSuccess) {
         // the stream is broken: wait for what was enqueued, fail the tickets
@@ -467,6 +504,7 @@ extern "C" edt_status edt_serve_destroy(edt_server* s)
         cudaStreamSynchronize(slot.stream);
         edt_plan_destroy(slot.plan);
         cudaEventDestroy(slot.done);
+        for (cudaEvent_t ev : slot.job_done) cudaEventDestroy(ev);
         cudaStreamDestroy(slot.stream);
     }
     if (s->pool) cudaMemPoolDestroy(s->pool);

@@ -527,10 +527,15 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
     specs = inputs.serving_jobs(pool_size, seed)
     with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
         pool = [torch.from_numpy(m).pin_memory() for m in ex.map(inputs.draw_job, specs)]
-    # result buffers (pinned) in power-of-two size classes, kept for reuse:
-    # up to `depth` jobs in flight without pinning depth x the largest job
+    # result buffers in power-of-two size classes, kept for reuse, carved
+    # from one pinned arena allocated up front (pinning memory while jobs run
+    # takes the driver for tens of milliseconds and stalls the server's
+    # calls): up to `depth` jobs in flight without pinning depth x the
+    # largest job
     depth = 64
     classes = {}
+    arena = torch.empty(8 << 30, dtype=torch.uint8).pin_memory()
+    arena_used = [0]
     srv = edt.Server(40 << 30, n_streams=3)
     busy = {}
 
@@ -545,6 +550,11 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
         lst = classes.setdefault(c, [])
         if lst:
             return c, lst.pop()
+        nb = 4 << c
+        if arena_used[0] + 2 * nb <= arena.numel():
+            o = arena_used[0]
+            arena_used[0] += 2 * nb
+            return c, (arena[o:o + nb].view(torch.int32), arena[o + nb:o + 2 * nb].view(torch.int32))
         return c, (torch.empty(1 << c, dtype=torch.int32).pin_memory(),
                    torch.empty(1 << c, dtype=torch.int32).pin_memory())
 
@@ -652,8 +662,8 @@ def measure_serve(edt, torch, n_jobs=20000, warm=1000, loads=(0.5, 0.8, 1.0), po
             "plain": "the same job stream, one synchronous edt_feature_host call per job",
             "sweep": runs,
             "note": f"{pool_size} distinct masks of the recipe (pinned, drawn untimed), each job one of them; "
-                    f"at most {depth} jobs in flight, their pinned result buffers reused in power-of-two size "
-                    f"classes; latency from the scheduled arrival"}
+                    f"at most {depth} jobs in flight, their result buffers reused in power-of-two size "
+                    f"classes carved from one pinned arena; latency from the scheduled arrival"}
 
 
 def run_reference(args, rank, world):
@@ -854,6 +864,10 @@ def run_gpu(args, rank, world, local_rank):
             extras["chamfer43"] = {"error": repr(exc)}
 
     if rank == 0:
+        try:
+            link = measure_host_link(torch, dev)
+        except Exception:  # noqa: BLE001 -- reported as absent
+            link = None
         peaks, peak_kind = measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         k2_avg_s = (k2_ms / max(k2_n, 1)) / 1e3
@@ -900,7 +914,12 @@ def run_gpu(args, rank, world, local_rank):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": H * W,
                     "d2h_bytes_per_step": 2 * 2 * 4 * H * W, "steps": e2e_steps,
                     "api": "edt_feature_pair_host, pinned host buffers",
-                    "calls_in_flight": 2, "one_call_at_a_time": e2e_serial},
+                    "calls_in_flight": 2, "one_call_at_a_time": e2e_serial,
+                    "host_link_gbs": link,
+                    "link_bound": None if not link else
+                    link["d2h"] * 1e9 / (2 * 2 * 4 * H * W / px_step) / 1e9,
+                    "link_bound_note": "the device-to-host rate over the results' bytes per pixel "
+                                       "(the copies in run beside them)"},
             "gpu_launches": k1_n + k2_n,
             "clocks": clocks,
             "extras": extras,
@@ -908,6 +927,25 @@ def run_gpu(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_host_link(torch, dev, nbytes=1 << 30, reps=3):
+    """Host link bandwidth: the best of `reps` copies of `nbytes` between a
+    pinned host buffer and device memory, each direction alone (GB/s)."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, dst, src in (("d2h", h, d), ("h2d", d, h)):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        out[name] = nbytes / min(ts) / 1e9
+    del h, d
+    return out
 
 
 def run_profile_workload(edt, torch, dev, which: str, calls: int, jobs: int = 4096):

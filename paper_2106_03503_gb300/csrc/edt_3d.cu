@@ -2,7 +2,9 @@
 // axis at a time;
 // for a [Dz][H][W] volume this library runs
 //   (z) the column pass along z: the volume seen as a 2-D image with Dz rows
-//       and H*W columns, handled by the same column-bit kernel as 2-D images;
+//       and H*W columns, handled by the same column-bit kernel as 2-D images,
+//       then (plain transforms) k_zoffsets, which writes every voxel's int16
+//       offset to its nearest source along z;
 //   (y) the lower envelope of Sec. 3.3.1 along y, over f(y') = (z - z')^2 with
 //       z' the nearest source along z in column (y', x): for each voxel it
 //       records the source (z', y') of its owning parabola, packed as
@@ -11,9 +13,9 @@
 //       from that record, writing D, F = z'*H*W + y'*W + x' and sqrt(D).
 // The (z', y') record lives in the caller's F (or D) buffer: the x pass reads
 // its rows into shared memory before it overwrites the same rows.
-// Both envelope passes use the band engine (edt_engine.cuh) with 32 lines per
-// block: 32 neighbouring x columns for the y pass (stores are coalesced across
-// lanes), 32 consecutive rows for the x pass (stores go through the tile).
+// A y tile (one z, 32 neighbouring x) or x unit (32 consecutive rows) whose
+// own distances are all small takes an exact direct search; the others take
+// the band engine (edt_engine.cuh) with one line per lane.
 #include "edt_engine.cuh"
 #include "edt_internal.h"
 

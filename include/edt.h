@@ -158,7 +158,7 @@ typedef struct edt_plan edt_plan;
 /* A batch plan owns the device scratch, a device job table and the CUDA graph
  * that run up to n_max jobs in one replay: 2-D jobs of any width edt_feature
  * accepts and 3-D jobs whose y and x lines fit the batched 3-D kernels'
- * shared memory (height up to about 1150, row width up to about 710; larger
+ * shared memory (height up to about 1150, row width up to about 670; larger
  * volumes: edt_feature).  `max_pixels` sizes the column-pass scratch the plan
  * allocates up front (about 0.26 bytes per pixel of 2-D jobs up to 2048 wide);
  * a batch that needs more grows it, which allocates and waits for the plan's

@@ -384,12 +384,16 @@ struct LineX {
     __device__ __forceinline__ int self_feature(int k) const { return (z * H + y) * W + k; }
 };
 
-// x unit: the records of its 32 rows, row rl at XPAD + rl * pitch words, the
-// pitch odd (lane = row reads of the hull engine hit distinct banks) and at
-// least W + XPAD, so that XPAD words of pad lie before every row and after the
-// last; then per-warp maxima (32 ints) and the engine.
+// x unit: the records of its 32 rows, row rl at xrow(rl) words: the pitch XP
+// is a multiple of 32 of at least W + XPAD + 31 words and row rl is shifted by
+// 8 (rl & 3) + (rl >> 2) words, so that at any column the 32 rows fall on 32
+// distinct banks (lane = row reads of the hull engine) and the 4 rows of a
+// group 8 banks apart (the 4 x 8 patches of the direct search).  At least
+// XPAD words of pad lie before every row and after the last.  Then per-warp
+// maxima (32 ints) and the engine.
 constexpr int XPAD = 96;
-__host__ __device__ static inline int xpass_pitch(int W) { return (W + XPAD) | 1; }
+__host__ __device__ static inline int xpass_pitch(int W) { return (W + XPAD + 31 + 31) & ~31; }
+__host__ __device__ static inline int xrow(int rl, int XP) { return XPAD + rl * XP + 8 * (rl & 3) + (rl >> 2); }
 __host__ __device__ static inline size_t xpass_rec_bytes(int W)
 {
     return ((size_t)(XPAD + 32 * xpass_pitch(W)) * 4 + 15) & ~size_t(15);
@@ -407,20 +411,19 @@ template <class Sync>
 __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t* P, int32_t* D, int32_t* F,
                            float* dist, int64_t row0, unsigned char* base, int tid, int nthr, int warp, Sync sync)
 {
-    const int pitch = xpass_pitch(W);
-    uint32_t* rec = reinterpret_cast<uint32_t*>(base) + XPAD;   // row rl at rec[rl * pitch]
+    const int XP = xpass_pitch(W);
+    uint32_t* rec = reinterpret_cast<uint32_t*>(base);   // row rl at rec[xrow(rl, XP)]
     int* wmax = reinterpret_cast<int*>(base + xpass_rec_bytes(W));
     const BandSmem sm = carve_band_smem(base + xpass_rec_bytes(W) + 128, NW, (1 << lg) >> 5);
     const int lane = tid & 31;
     const int64_t nrows = (int64_t)Dz * H;
 
-    // the pads (before row 0 and after every row) cost 0xFFFF to the direct
-    // search below, more than any answer it accepts
-    for (int t = tid; t < 33 * (XPAD + 1); t += nthr) {
-        const int g = t / (XPAD + 1), o = t - g * (XPAD + 1);
-        const int start = g == 0 ? -XPAD : (g - 1) * pitch + W;
-        const int end = g == 0 ? 0 : (g == 32 ? 31 * pitch + W + XPAD : g * pitch);
-        if (start + o < end) rec[start + o] = 0xFFFFu;
+    // the pads (before row 0, between rows, after the last) cost 0xFFFF to
+    // the direct search below, more than any answer it accepts
+    for (int g = warp; g <= 32; g += NW) {
+        const int st = g == 0 ? 0 : xrow(g - 1, XP) + W;
+        const int en = g == 32 ? xrow(31, XP) + W + XPAD : xrow(g, XP);
+        for (int a = st + lane; a < en; a += 32) rec[a] = 0xFFFFu;
     }
     // the rows' (z', y') records, and the largest (z, y) distance among them
     // (rows past the volume's end count as 0); the (z, y) of RU rows at a time
@@ -452,7 +455,7 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
                     dmax = max(dmax, p[i] == PNONE ? 32767 : max(abs(dz), abs(dy)));
                     q = xrec_encode(p[i], zr[i], yr[i]);
                 }
-                rec[(rl0 + i) * pitch + k] = q;
+                rec[xrow(rl0 + i, XP) + k] = q;
             }
         }
     }
@@ -462,50 +465,46 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
     for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
 
     if (dmax <= DIRECT_MAX_DIST) {
-        // near answers: each warp takes whole rows, its lanes 32 consecutive
-        // x, and searches outward along the row (Eq. (5) minimised exactly,
-        // rightmost x' at a tie, as the hull walk); every candidate at most
-        // about 91 positions away, so the search stays short, neighbouring
-        // lanes search about as far, and D, F, dist go out as 128-byte lines
-        for (int rl = warp; rl < 32; rl += NW) {
+        // near answers: each position searches outward along its row (Eq.
+        // (5) minimised exactly, rightmost x' at a tie, as the hull walk), two
+        // steps per test of the stop rule (a step past the stop costs at least
+        // its r^2, more than the best, and changes nothing).  Every record of
+        // this unit has its offsets within +-64, so bits 15..0 are its
+        // squared length (xrec_encode); the best is at most 2 * 64^2, so a
+        // search stops by r = 91 < XPAD and every look past a row's ends reads
+        // a pad.  A warp takes patches of 4 rows x 8 x: a search runs as far
+        // as the farthest lane of its warp, and neighbours in both directions
+        // need more alike distances than 32 along x alone.
+        const int items = 8 * ((W + 7) >> 3);
+        for (int it = warp; it < items; it += NW) {
+            const int rl = 4 * (it & 7) + (lane >> 3), j = 8 * (it >> 3) + (lane & 7);
             const int64_t row = row0 + rl;
-            if (row >= nrows) break;
-            const int zz = (int)(row / H), yy = (int)(row % H);
-            const uint32_t* rr = rec + rl * pitch;
-            // every record of this unit has its offsets within +-64, so bits
-            // 15..0 are its squared length (xrec_encode).  The search takes
-            // two steps per test of the stop rule (a step past the stop costs
-            // at least its r^2, more than the best, and changes nothing); the
-            // best is at most 2 * 64^2, so it stops by r = 91 < XPAD and every
-            // look past the row's ends reads a pad.
-            for (int c0 = 0; c0 < W; c0 += 32) {
-                const int j = c0 + lane;
-                if (j >= W) continue;
-                int best = (int)(rr[j] & 0xFFFFu), bk = j;
-                for (int r = 1, r2 = 1; r2 <= best; r += 2, r2 += 4 * r - 4) {
-                    const int r2b = r2 + 2 * r + 1;
-                    const int cl = (int)(rr[j - r] & 0xFFFFu) + r2, cr = (int)(rr[j + r] & 0xFFFFu) + r2;
-                    const int cl2 = (int)(rr[j - r - 1] & 0xFFFFu) + r2b;
-                    const int cr2 = (int)(rr[j + r + 1] & 0xFFFFu) + r2b;
-                    if (cl < best) { best = cl; bk = j - r; }
-                    if (cr <= best) { best = cr; bk = j + r; }
-                    if (cl2 < best) { best = cl2; bk = j - r - 1; }
-                    if (cr2 <= best) { best = cr2; bk = j + r + 1; }
-                }
-                const uint32_t p = rr[bk];
-                const int dz = (int)(int8_t)(p >> 24), dy = (int)(int8_t)((p >> 16) & 0xFFu);
-                const int64_t q = row * W + j;
-                if (D) D[q] = best;
-                if (F) F[q] = ((zz - dz) * H + (yy - dy)) * W + bk;
-                if (dist) dist[q] = sqrt_rn_int(best);
+            if (row >= nrows || j >= W) continue;
+            const uint32_t* rr = rec + xrow(rl, XP);
+            int best = (int)(rr[j] & 0xFFFFu), bk = j;
+            for (int r = 1, r2 = 1; r2 <= best; r += 2, r2 += 4 * r - 4) {
+                const int r2b = r2 + 2 * r + 1;
+                const int cl = (int)(rr[j - r] & 0xFFFFu) + r2, cr = (int)(rr[j + r] & 0xFFFFu) + r2;
+                const int cl2 = (int)(rr[j - r - 1] & 0xFFFFu) + r2b;
+                const int cr2 = (int)(rr[j + r + 1] & 0xFFFFu) + r2b;
+                if (cl < best) { best = cl; bk = j - r; }
+                if (cr <= best) { best = cr; bk = j + r; }
+                if (cl2 < best) { best = cl2; bk = j - r - 1; }
+                if (cr2 <= best) { best = cr2; bk = j + r + 1; }
             }
+            const uint32_t p = rr[bk];
+            const int dz = (int)(int8_t)(p >> 24), dy = (int)(int8_t)((p >> 16) & 0xFFu);
+            const int64_t q = row * W + j;
+            if (D) D[q] = best;
+            if (F) F[q] = (int)((row - (int64_t)dz * H - dy) * W + bk);   // row = z * H + y
+            if (dist) dist[q] = sqrt_rn_int(best);
         }
         return;
     }
 
     const int64_t row = row0 + lane;
     LineX line;
-    line.rec = rec + lane * pitch;
+    line.rec = rec + xrow(lane, XP);
     line.z = (int)(row / H);
     line.y = (int)(row % H);
     line.H = H;

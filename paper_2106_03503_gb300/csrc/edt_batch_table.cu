@@ -50,7 +50,7 @@ int batch_kind(const edt_job& j, const char** why)
         }
         batch_line_geometry(W, pos, lg, NW);
         if (batch_xpass_group_bytes(W, lg, NW) > BATCH_3D_SMEM) {
-            if (why) *why = "3-D row width too large for the batched x pass (about 710 at most)";
+            if (why) *why = "3-D row width too large for the batched x pass (about 670 at most)";
             return -1;
         }
     }

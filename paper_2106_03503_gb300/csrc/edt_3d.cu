@@ -88,15 +88,15 @@ struct OutY {
     }
 };
 
-// y tile: z offsets of [YPAD + H + YPAD][YP] (int16), per-warp maxima (32
-// ints), engine
+// y tile: z offsets of [YPAD + H + YPAD][YP] (int16), per-warp maxima and
+// counts (2 x 32 ints), the direct search's give-up flag (16 bytes), engine
 __host__ __device__ static inline size_t ytile_bytes(int H)
 {
     return ((size_t)(H + 2 * YPAD) * YP * 2 + 15) & ~size_t(15);
 }
 __host__ __device__ static inline size_t ypass_smem(int H, int lg, int NW)
 {
-    return ytile_bytes(H) + 128 + band_smem_bytes(NW, (1 << lg) >> 5);
+    return ytile_bytes(H) + 272 + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
 size_t batch_ypass_group_bytes(int H, int lg, int NW) { return ypass_smem(H, lg, NW); }
@@ -160,6 +160,58 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// Direct search of a y tile: each position searches outward along y (Eq.
+// (5) minimised exactly, rightmost y' at a tie, as the hull walk), two steps
+// per test of the stop rule (a step past the stop costs at least its r^2,
+// more than the best, and changes nothing).  A warp takes patches of 4 y x 8
+// x: a search runs as far as the farthest lane of its warp, and neighbours in
+// both directions need more alike distances than 32 along x alone.  Without
+// CHECK every own offset is at most DIRECT_MAX_DIST, so a search stops by
+// r = DIRECT_MAX_DIST + 1 < YPAD and never leaves the padded tile (a pad or a
+// column without source costs 32767^2, more than any answer).  With CHECK
+// (some own offset larger, or a column without source) the searches stop at
+// that distance, and a search still open there makes the whole tile give up
+// (returns false; the caller then runs the band engine, which rewrites every
+// position with the same value).
+template <bool CHECK, class Sync>
+__device__ bool ydirect(const short* gz, int H, int W, int x0, int z, int64_t plane, uint32_t* __restrict__ P,
+                        int lane, int warp, int NW, volatile int* abort, Sync sync)
+{
+    const int items = 4 * ((H + 3) >> 2);
+    for (int it = warp; it < items; it += NW) {
+        if (CHECK && __any_sync(FULL, *abort != 0)) break;   // the same decision in every lane
+        const int j = 4 * (it >> 2) + (lane >> 3), xt = 8 * (it & 3) + (lane & 7);
+        const bool act = j < H && x0 + xt < W;   // a voxel of the tile
+        const short* col = gz + xt;
+        int best = 0, bk = j, rn2 = 1;
+        if (act) {
+            const int d0 = col[j * YP];
+            best = d0 * d0;
+            int r = 1, r2 = 1;
+            for (; r2 <= best && (!CHECK || r < DIRECT_MAX_DIST); r += 2, r2 += 4 * r - 4) {
+                const int r2b = r2 + 2 * r + 1;
+                const int dl = col[(j - r) * YP], dr = col[(j + r) * YP];
+                const int dl2 = col[(j - r - 1) * YP], dr2 = col[(j + r + 1) * YP];
+                const int cl = dl * dl + r2, cr = dr * dr + r2;
+                const int cl2 = dl2 * dl2 + r2b, cr2 = dr2 * dr2 + r2b;
+                if (cl < best) { best = cl; bk = j - r; }
+                if (cr <= best) { best = cr; bk = j + r; }
+                if (cl2 < best) { best = cl2; bk = j - r - 1; }
+                if (cr2 <= best) { best = cr2; bk = j + r + 1; }
+            }
+            rn2 = r2;   // r^2 of the nearest distance not searched
+        }
+        if (CHECK && __any_sync(FULL, act && rn2 <= best)) {
+            *abort = 1;
+            break;
+        }
+        if (act) P[(int64_t)z * plane + (int64_t)j * W + x0 + xt] = ((uint32_t)(z + col[bk * YP]) << 16) | (uint32_t)bk;
+    }
+    if (!CHECK) return true;
+    sync();
+    return *abort == 0;
+}
+
 // One y-pass tile: plane z, the 32 columns x0 .. x0+31 (one line per lane),
 // NW warps = y segments.  Run by the nthr threads of one engine (tid = thread
 // within it, warp = warp within it) over the shared memory at `base`.  The z
@@ -172,7 +224,10 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, const short* __res
 {
     short* gz = reinterpret_cast<short*>(base) + YPAD * YP;     // row 0 of the tile
     int* wmax = reinterpret_cast<int*>(base + ytile_bytes(H));
-    const BandSmem sm = carve_band_smem(base + ytile_bytes(H) + 128, NW, (1 << lg) >> 5);
+    int* wfar = wmax + 32;
+    volatile int* abort = wmax + 64;
+    const BandSmem sm = carve_band_smem(base + ytile_bytes(H) + 272, NW, (1 << lg) >> 5);
+    if (tid == 0) *abort = 0;   // seen by all after the barrier below
     const int lane = tid & 31;
     const int64_t plane = (int64_t)H * W;
     const int zb = z >> 5, zr = z & 31, zG = zb >> s.gs;
@@ -190,7 +245,7 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, const short* __res
     const uint32_t* Uz = s.U + (int64_t)zb * plane;
     const int total = H * 32;
     constexpr int SU = 4;
-    int dmax = 0;
+    int dmax = 0, far = 0;   // largest |offset|, and how many exceed DIRECT_MAX_DIST
     if (d16 && (W & 7) == 0) {
         // 8 offsets per 16-byte chunk (every row starts 16-byte aligned): all
         // of a thread's chunks copied asynchronously at once, chunks past the
@@ -211,9 +266,12 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, const short* __res
             const int y = e >> 2, xq = (e & 3) * 8;
             if (x0 + xq >= W) continue;
             const uint4 v = *reinterpret_cast<const uint4*>(gz + y * YP + xq);
-            const uint32_t m = __vmaxs2(__vmaxs2(__vabsss2(v.x), __vabsss2(v.y)),
-                                        __vmaxs2(__vabsss2(v.z), __vabsss2(v.w)));
+            const uint32_t a[4] = {__vabsss2(v.x), __vabsss2(v.y), __vabsss2(v.z), __vabsss2(v.w)};
+            const uint32_t m = __vmaxs2(__vmaxs2(a[0], a[1]), __vmaxs2(a[2], a[3]));
             dmax = max(dmax, (int)max(m & 0xFFFFu, m >> 16));
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                far += (int)((a[t] & 0xFFFFu) > (uint32_t)DIRECT_MAX_DIST) + (int)((a[t] >> 16) > (uint32_t)DIRECT_MAX_DIST);
         }
     } else if (d16) {
         // W not a multiple of 8: offset by offset
@@ -224,6 +282,7 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, const short* __res
             if (x0 + xl < W) {
                 d = src[(int64_t)y * W + xl];
                 dmax = max(dmax, abs(d));
+                far += abs(d) > DIRECT_MAX_DIST;
             }
             gz[y * YP + xl] = (short)d;
         }
@@ -256,47 +315,34 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, const short* __res
                 const int g = nearest_in_column(w[i], zb * 32, zr, (int)up, (int)dn);
                 d = g < 0 ? YNONE : g - z;
                 dmax = max(dmax, abs(d));
+                far += abs(d) > DIRECT_MAX_DIST;
             }
             gz[(e >> 5) * YP + (e & 31)] = (short)d;
         }
     }
     dmax = (int)__reduce_max_sync(FULL, (unsigned)dmax);
-    if (lane == 0) wmax[warp] = dmax;
+    far = (int)__reduce_add_sync(FULL, (unsigned)far);
+    if (lane == 0) {
+        wmax[warp] = dmax;
+        wfar[warp] = far;
+    }
     sync();
-    for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
+    far = 0;
+    for (int w = 0; w < NW; ++w) {
+        dmax = max(dmax, wmax[w]);
+        far += wfar[w];
+    }
 
-    if (dmax <= DIRECT_MAX_DIST) {
-        // near answers: each position searches outward along y (Eq. (5)
-        // minimised exactly, rightmost y' at a tie, as the hull walk), two
-        // steps per test of the stop rule (a step past the stop costs at least
-        // its r^2, more than the best, and changes nothing); every own offset
-        // is at most DIRECT_MAX_DIST, so the search stops by r = DIRECT_MAX_DIST
-        // + 1 < YPAD, never leaves the padded tile and needs no bounds or
-        // validity test (a pad or a column without source costs 32767^2, more
-        // than any answer).  A warp takes patches of 4 y x 8 x: a search runs
-        // as far as the farthest lane of its warp, and neighbours in both
-        // directions need more alike distances than 32 along x alone.
-        const int items = 4 * ((H + 3) >> 2);
-        for (int it = warp; it < items; it += NW) {
-            const int j = 4 * (it >> 2) + (lane >> 3), xt = 8 * (it & 3) + (lane & 7);
-            if (j >= H || x0 + xt >= W) continue;   // not a voxel of the tile
-            const short* col = gz + xt;
-            const int d0 = col[j * YP];
-            int best = d0 * d0, bk = j;
-            for (int r = 1, r2 = 1; r2 <= best; r += 2, r2 += 4 * r - 4) {
-                const int r2b = r2 + 2 * r + 1;
-                const int dl = col[(j - r) * YP], dr = col[(j + r) * YP];
-                const int dl2 = col[(j - r - 1) * YP], dr2 = col[(j + r + 1) * YP];
-                const int cl = dl * dl + r2, cr = dr * dr + r2;
-                const int cl2 = dl2 * dl2 + r2b, cr2 = dr2 * dr2 + r2b;
-                if (cl < best) { best = cl; bk = j - r; }
-                if (cr <= best) { best = cr; bk = j + r; }
-                if (cl2 < best) { best = cl2; bk = j - r - 1; }
-                if (cr2 <= best) { best = cr2; bk = j + r + 1; }
-            }
-            P[(int64_t)z * plane + (int64_t)j * W + x0 + xt] = ((uint32_t)(z + col[bk * YP]) << 16) | (uint32_t)bk;
-        }
-    } else {
+    // every own offset near: the direct search always ends inside the tile;
+    // some far: it is tried while at most half of the tile's offsets are far
+    // (beyond that the searches mostly run to their limit and give up)
+    const int entries = H * min(32, W - x0);
+    bool done = false;
+    if (dmax <= DIRECT_MAX_DIST)
+        done = ydirect<false>(gz, H, W, x0, z, plane, P, lane, warp, NW, abort, sync);
+    else if (2 * far <= entries)
+        done = ydirect<true>(gz, H, W, x0, z, plane, P, lane, warp, NW, abort, sync);
+    if (!done) {
         const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
         const LineY line{gz, lane, z};
         band_envelope(line, out, sm, H, lg, NW, nullptr, warp, sync);
@@ -390,7 +436,8 @@ struct LineX {
 // distinct banks (lane = row reads of the hull engine) and the 4 rows of a
 // group 8 banks apart (the 4 x 8 patches of the direct search).  At least
 // XPAD words of pad lie before every row and after the last.  Then per-warp
-// maxima (32 ints) and the engine.
+// maxima (32 ints), the direct search's give-up flag (16 bytes) and the
+// engine.
 constexpr int XPAD = 96;
 __host__ __device__ static inline int xpass_pitch(int W) { return (W + XPAD + 31 + 31) & ~31; }
 __host__ __device__ static inline int xrow(int rl, int XP) { return XPAD + rl * XP + 8 * (rl & 3) + (rl >> 2); }
@@ -400,10 +447,70 @@ __host__ __device__ static inline size_t xpass_rec_bytes(int W)
 }
 __host__ __device__ static inline size_t xpass_smem(int W, int lg, int NW)
 {
-    return xpass_rec_bytes(W) + 128 + band_smem_bytes(NW, (1 << lg) >> 5);
+    return xpass_rec_bytes(W) + 144 + band_smem_bytes(NW, (1 << lg) >> 5);
 }
 
 size_t batch_xpass_group_bytes(int W, int lg, int NW) { return xpass_smem(W, lg, NW); }
+
+// Direct search of an x unit: each position searches outward along its row
+// (Eq. (5) minimised exactly, rightmost x' at a tie, as the hull walk), two
+// steps per test of the stop rule (a step past the stop costs at least its
+// r^2, more than the best, and changes nothing), a candidate's cost being its
+// record's bits 15..0 (xrec_encode).  A warp takes patches of 4 rows x 8 x: a
+// search runs as far as the farthest lane of its warp, and neighbours in both
+// directions need more alike distances than 32 along x alone.  Without CHECK
+// every record's offsets are within +-64, bits 15..0 are the squared length
+// (at most 2 * 64^2), so a search stops by r = 91 < XPAD and every look past a
+// row's ends reads a pad.  With CHECK (larger offsets, or planes without
+// source) bits 15..0 of an escape record or of PNONE are 32768 or more, below
+// its true cost only when that is 128^2 or more; the searches stop at r = 91,
+// and a search still open there (its best 91^2 or more, so any record whose
+// bits 15..0 are not its true cost could still matter) makes the whole unit
+// give up (returns false; the caller then runs the band engine).
+template <bool CHECK, class Sync>
+__device__ bool xdirect(const uint32_t* rec, int XP, int H, int W, int64_t row0, int64_t nrows, int32_t* D,
+                        int32_t* F, float* dist, int lane, int warp, int NW, volatile int* abort, Sync sync)
+{
+    const int items = 8 * ((W + 7) >> 3);
+    for (int it = warp; it < items; it += NW) {
+        if (CHECK && __any_sync(FULL, *abort != 0)) break;   // the same decision in every lane
+        const int rl = 4 * (it & 7) + (lane >> 3), j = 8 * (it >> 3) + (lane & 7);
+        const int64_t row = row0 + rl;
+        const bool act = row < nrows && j < W;
+        const uint32_t* rr = rec + xrow(rl, XP);
+        int best = 0, bk = j, rn2 = 1;
+        if (act) {
+            best = (int)(rr[j] & 0xFFFFu);
+            int r = 1, r2 = 1;
+            for (; r2 <= best && (!CHECK || r < 90); r += 2, r2 += 4 * r - 4) {
+                const int r2b = r2 + 2 * r + 1;
+                const int cl = (int)(rr[j - r] & 0xFFFFu) + r2, cr = (int)(rr[j + r] & 0xFFFFu) + r2;
+                const int cl2 = (int)(rr[j - r - 1] & 0xFFFFu) + r2b;
+                const int cr2 = (int)(rr[j + r + 1] & 0xFFFFu) + r2b;
+                if (cl < best) { best = cl; bk = j - r; }
+                if (cr <= best) { best = cr; bk = j + r; }
+                if (cl2 < best) { best = cl2; bk = j - r - 1; }
+                if (cr2 <= best) { best = cr2; bk = j + r + 1; }
+            }
+            rn2 = r2;   // r^2 of the nearest distance not searched
+        }
+        if (CHECK && __any_sync(FULL, act && rn2 <= best)) {
+            *abort = 1;
+            break;
+        }
+        if (act) {
+            const uint32_t p = rr[bk];
+            const int dz = (int)(int8_t)(p >> 24), dy = (int)(int8_t)((p >> 16) & 0xFFu);
+            const int64_t q = row * W + j;
+            if (D) D[q] = best;
+            if (F) F[q] = (int)((row - (int64_t)dz * H - dy) * W + bk);   // row = z * H + y
+            if (dist) dist[q] = sqrt_rn_int(best);
+        }
+    }
+    if (!CHECK) return true;
+    sync();
+    return *abort == 0;
+}
 
 // One x-pass unit: the 32 rows (z, y) starting at row0 of the Dz*H rows (one
 // per lane), NW warps = x segments; run by one engine as ypass_tile.
@@ -414,7 +521,9 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
     const int XP = xpass_pitch(W);
     uint32_t* rec = reinterpret_cast<uint32_t*>(base);   // row rl at rec[xrow(rl, XP)]
     int* wmax = reinterpret_cast<int*>(base + xpass_rec_bytes(W));
-    const BandSmem sm = carve_band_smem(base + xpass_rec_bytes(W) + 128, NW, (1 << lg) >> 5);
+    volatile int* abort = wmax + 32;
+    const BandSmem sm = carve_band_smem(base + xpass_rec_bytes(W) + 144, NW, (1 << lg) >> 5);
+    if (tid == 0) *abort = 0;   // seen by all after the barrier below
     const int lane = tid & 31;
     const int64_t nrows = (int64_t)Dz * H;
 
@@ -464,43 +573,10 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
     sync();
     for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
 
-    if (dmax <= DIRECT_MAX_DIST) {
-        // near answers: each position searches outward along its row (Eq.
-        // (5) minimised exactly, rightmost x' at a tie, as the hull walk), two
-        // steps per test of the stop rule (a step past the stop costs at least
-        // its r^2, more than the best, and changes nothing).  Every record of
-        // this unit has its offsets within +-64, so bits 15..0 are its
-        // squared length (xrec_encode); the best is at most 2 * 64^2, so a
-        // search stops by r = 91 < XPAD and every look past a row's ends reads
-        // a pad.  A warp takes patches of 4 rows x 8 x: a search runs as far
-        // as the farthest lane of its warp, and neighbours in both directions
-        // need more alike distances than 32 along x alone.
-        const int items = 8 * ((W + 7) >> 3);
-        for (int it = warp; it < items; it += NW) {
-            const int rl = 4 * (it & 7) + (lane >> 3), j = 8 * (it >> 3) + (lane & 7);
-            const int64_t row = row0 + rl;
-            if (row >= nrows || j >= W) continue;
-            const uint32_t* rr = rec + xrow(rl, XP);
-            int best = (int)(rr[j] & 0xFFFFu), bk = j;
-            for (int r = 1, r2 = 1; r2 <= best; r += 2, r2 += 4 * r - 4) {
-                const int r2b = r2 + 2 * r + 1;
-                const int cl = (int)(rr[j - r] & 0xFFFFu) + r2, cr = (int)(rr[j + r] & 0xFFFFu) + r2;
-                const int cl2 = (int)(rr[j - r - 1] & 0xFFFFu) + r2b;
-                const int cr2 = (int)(rr[j + r + 1] & 0xFFFFu) + r2b;
-                if (cl < best) { best = cl; bk = j - r; }
-                if (cr <= best) { best = cr; bk = j + r; }
-                if (cl2 < best) { best = cl2; bk = j - r - 1; }
-                if (cr2 <= best) { best = cr2; bk = j + r + 1; }
-            }
-            const uint32_t p = rr[bk];
-            const int dz = (int)(int8_t)(p >> 24), dy = (int)(int8_t)((p >> 16) & 0xFFu);
-            const int64_t q = row * W + j;
-            if (D) D[q] = best;
-            if (F) F[q] = (int)((row - (int64_t)dz * H - dy) * W + bk);   // row = z * H + y
-            if (dist) dist[q] = sqrt_rn_int(best);
-        }
-        return;
-    }
+    const bool done = dmax <= DIRECT_MAX_DIST
+                          ? xdirect<false>(rec, XP, H, W, row0, nrows, D, F, dist, lane, warp, NW, abort, sync)
+                          : xdirect<true>(rec, XP, H, W, row0, nrows, D, F, dist, lane, warp, NW, abort, sync);
+    if (done) return;
 
     const int64_t row = row0 + lane;
     LineX line;

@@ -12,6 +12,9 @@
 // TMA tile stores and 32-byte vector stores are carried out in C++ with the
 // hardware's alignment and bounds rules checked.
 #include "shim.h"
+// the runtime defines the votes themselves (the shim's macros are for kernel sources)
+#undef __any_sync
+#undef __ballot_sync
 #include <ucontext.h>
 #include <sanitizer/common_interface_defs.h>
 
@@ -116,6 +119,11 @@ static unsigned ballot_tag(int pred, const void* tag)
 }
 unsigned __ballot_sync(unsigned, int pred) { return ballot_tag(pred, __builtin_return_address(0)); }
 int __any_sync(unsigned, int pred) { return ballot_tag(pred, __builtin_return_address(0)) != 0; }
+unsigned emu_ballot_at(int pred, const char* file, int line)
+{
+    // a site tag from the file name's address and the line
+    return ballot_tag(pred, reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(file) * 65599u + (uintptr_t)line));
+}
 unsigned __reduce_and_sync(unsigned, unsigned v)
 {
     const int t = g_f[g_cur].tid;
@@ -133,6 +141,16 @@ unsigned __reduce_max_sync(unsigned, unsigned v)
     warp_wait(__builtin_return_address(0));
     unsigned r = 0u;
     for (int l = 0; l < 32; ++l) r = g_slot[t >> 5][l] > r ? g_slot[t >> 5][l] : r;
+    warp_wait(__builtin_return_address(0));
+    return r;
+}
+unsigned __reduce_add_sync(unsigned, unsigned v)
+{
+    const int t = g_f[g_cur].tid;
+    g_slot[t >> 5][t & 31] = v;
+    warp_wait(__builtin_return_address(0));
+    unsigned r = 0u;
+    for (int l = 0; l < 32; ++l) r += g_slot[t >> 5][l];
     warp_wait(__builtin_return_address(0));
     return r;
 }

@@ -100,7 +100,15 @@ unsigned __shfl_xor_sync(unsigned mask, unsigned v, int lanemask);
 unsigned __ballot_sync(unsigned mask, int pred);
 unsigned __reduce_and_sync(unsigned mask, unsigned v);
 unsigned __reduce_max_sync(unsigned mask, unsigned v);
+unsigned __reduce_add_sync(unsigned mask, unsigned v);
 int __any_sync(unsigned mask, int pred);
+// A warp vote is one convergence point per source site, as on the GPU: the
+// host compiler may duplicate the call into divergent paths, so votes from
+// kernel sources carry their file and line as the site instead of the
+// return address.
+unsigned emu_ballot_at(int pred, const char* file, int line);
+#define __any_sync(mask, pred) (emu_ballot_at((pred), __FILE__, __LINE__) != 0u)
+#define __ballot_sync(mask, pred) emu_ballot_at((pred), __FILE__, __LINE__)
 unsigned char* emu_smem();
 size_t emu_smem_bytes();
 void emu_launch(unsigned blocks, unsigned threads, size_t smem, std::function<void()> body);

@@ -296,7 +296,9 @@ def measure_batch(edt, torch, dev, reps=5):
     layout; the C call still sorts and fills its table each time) vs one
     edt_feature call per mask, both on one stream, GPU time by CUDA events
     around the whole batch (L2 not flushed: the batch is 1.2 Gpixel, far
-    larger than L2)."""
+    larger than L2).  The batch geometry is the batch autotuner's (untimed,
+    before the timed replays); the built-in geometry's time is reported
+    beside it."""
     from paper_2106_03503_gb300 import inputs
     masks_np = inputs.batch_4096()
     masks = [torch.from_numpy(m).to(dev) for m in masks_np]
@@ -327,6 +329,10 @@ def measure_batch(edt, torch, dev, reps=5):
 
     t_plain = timed(plain)
     prepared = plan.prepare(jobs)            # the job table, filled once for the fixed batch layout
+    t_builtin = timed(lambda: plan.run(prepared))
+    t0 = time.perf_counter()
+    plan.autotune(prepared)                  # untimed: the batch autotuner's geometry per shape class
+    tune_s = time.perf_counter() - t0
     t_batch = timed(lambda: plan.run(prepared))
     plan.close()
     import oracle
@@ -338,6 +344,9 @@ def measure_batch(edt, torch, dev, reps=5):
             "pixels": px, "plain_ms": t_plain, "batched_ms": t_batch,
             "plain_gpx_s": px / (t_plain / 1e3) / 1e9, "batched_gpx_s": px / (t_batch / 1e3) / 1e9,
             "speedup": t_plain / t_batch,
+            "builtin_geometry_ms": t_builtin, "autotune_s": tune_s,
+            "geometry": "edt_autotune_batch's (untimed, before the timed replays; it keeps the built-in "
+                        "geometry unless its choices make the whole batch faster)",
             "plain": "one edt_feature call per mask from Python (ctypes) on one stream",
             "cpu_oracle": cpu}
 

@@ -184,6 +184,8 @@ static edt_status check_batch(const edt_job* jobs, int n)
 
 namespace edt {
 
+int plan_n_max(const edt_plan* p) { return p->n_max; }
+
 // Enqueue a validated batch; scratch: the column-pass scratch to use (device,
 // at least batch_layout's bytes), or NULL for the plan's own.
 edt_status batch_enqueue(edt_plan* p, const edt_job* jobs, int n, char* scratch, cudaStream_t stream)

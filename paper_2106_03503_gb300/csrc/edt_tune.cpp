@@ -9,8 +9,9 @@
 // class.  edt_autotune_batch does the same for the geometry of the batch
 // kernels (the smallest row segment of narrow 2-D jobs, the positions per warp
 // of the 3-D y and x passes), timing each shape class of the caller's batch
-// on its own.  A choice never changes a result: every segmentation gives the
-// same D and F, bit for bit.
+// on its own, then keeping those choices only if the whole batch runs faster
+// with them than with the built-in geometry.  A choice never changes a
+// result: every segmentation gives the same D and F, bit for bit.
 #include <algorithm>
 #include <array>
 #include <cstdio>
@@ -84,6 +85,7 @@ void batch_tuning_store(int ndim, const int* shape, const BatchTuning& t)
 }
 
 edt_status batch_enqueue(edt_plan* p, const edt_job* jobs, int n, char* scratch, cudaStream_t stream);
+int plan_n_max(const edt_plan* p);
 
 }  // namespace edt
 
@@ -171,6 +173,9 @@ extern "C" edt_status edt_autotune(const uint8_t* mask, int ndim, const int* sha
 extern "C" edt_status edt_autotune_batch(edt_plan* plan, const edt_job* jobs, int n, edt_stream_t stream_)
 {
     if (!plan || !jobs || n <= 0) return fail(EDT_ERR_INVALID, "plan, jobs and n > 0 are required");
+    const int n_max = plan_n_max(plan);
+    if (n > n_max) return fail(EDT_ERR_INVALID, "%d jobs exceed the plan's %d", n, n_max);
+    const int chunk = std::min(256, n_max);   // jobs per timed replay
     cudaStream_t stream = (cudaStream_t)stream_;
     for (int i = 0; i < n; ++i) {
         edt_status st = check_shape(jobs[i].ndim, jobs[i].shape, jobs[i].mode);
@@ -196,8 +201,8 @@ extern "C" edt_status edt_autotune_batch(edt_plan* plan, const edt_job* jobs, in
         auto time_with = [&](const BatchTuning& t) -> float {
             batch_tuning_store(j0.ndim, j0.shape, t);
             float total = 0.f;
-            for (size_t off = 0; off < cj.size(); off += (size_t)256) {
-                const int cnt = (int)std::min<size_t>(256, cj.size() - off);
+            for (size_t off = 0; off < cj.size(); off += (size_t)chunk) {
+                const int cnt = (int)std::min<size_t>((size_t)chunk, cj.size() - off);
                 if (batch_enqueue(plan, cj.data() + off, cnt, nullptr, stream) != EDT_OK) return -1.f;
                 cudaEventRecord(ev[0], stream);
                 for (int r = 0; r < 3; ++r)
@@ -242,6 +247,32 @@ extern "C" edt_status edt_autotune_batch(edt_plan* plan, const edt_job* jobs, in
             }
         }
         batch_tuning_store(j0.ndim, j0.shape, st == EDT_OK ? best : BatchTuning{});
+    }
+    // the classes were timed alone, where a replay's fixed costs weigh more
+    // than in the whole batch: keep the choices only if the whole batch is
+    // faster with them than with the built-in geometry
+    if (st == EDT_OK) {
+        auto time_all = [&]() -> float {
+            if (batch_enqueue(plan, jobs, n, nullptr, stream) != EDT_OK) return -1.f;   // warm
+            cudaEventRecord(ev[0], stream);
+            for (int r = 0; r < 3; ++r)
+                if (batch_enqueue(plan, jobs, n, nullptr, stream) != EDT_OK) return -1.f;
+            cudaEventRecord(ev[1], stream);
+            if (cudaEventSynchronize(ev[1]) != cudaSuccess) return -1.f;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            return ms;
+        };
+        std::map<Key, BatchTuning> chosen;
+        for (auto& kv : classes) chosen[kv.first] = batch_tuning_lookup(kv.second[0].ndim, kv.second[0].shape);
+        const float t_chosen = time_all();
+        for (auto& kv : classes) batch_tuning_store(kv.second[0].ndim, kv.second[0].shape, BatchTuning{});
+        const float t_builtin = time_all();
+        if (t_chosen < 0 || t_builtin < 0) {
+            st = fail(EDT_ERR_CUDA, "autotune_batch: timing the whole batch failed");
+        } else if (t_chosen < t_builtin) {
+            for (auto& kv : classes) batch_tuning_store(kv.second[0].ndim, kv.second[0].shape, chosen[kv.first]);
+        }
     }
     e = cudaStreamSynchronize(stream);
     if (st == EDT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");

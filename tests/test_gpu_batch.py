@@ -93,6 +93,9 @@ def test_batch_errors():
     with pytest.raises(edt.EdtError):
         plan.run([(m, 0, None, F, None)] * 3)            # more jobs than n_max
     with pytest.raises(edt.EdtError) as e:
+        plan.autotune([(m, 0, None, F, None)] * 3)       # the autotuner's batches must fit the plan too
+    assert e.value.status == 1
+    with pytest.raises(edt.EdtError) as e:
         plan.run([(m, 5, None, F, None)])                # bad mode
     assert e.value.status == 1
     plan.close()

@@ -85,6 +85,27 @@ def test_3d_smoothed_blobs():
         check_against_oracle(m, mode)
 
 
+@pytest.mark.parametrize("p", [0.001, 0.003, 0.01])
+def test_3d_sparse_sides_above_128(p):
+    """Sparse volumes with every side above 128: z and y offsets beyond the
+    direct searches' guarantee (tiles and units that try the search and give
+    up to the hull, or settle), and x-pass records whose offsets need the
+    escape form."""
+    m = inputs.bernoulli_mask((160, 200, 176), p, 4100 + int(p * 1e4))
+    for mode in (0, 1):
+        check_against_oracle(m, mode)
+
+
+def test_3d_blobs_with_empty_slabs():
+    """Smoothed-noise blobs with empty z slabs and an empty y band: near and
+    far own offsets side by side in the same tiles and units."""
+    m = inputs.smoothed_noise_volume((192, 144, 160), 4.0, 35).copy()
+    m[40:140] = 0
+    m[:, 60:130] = 0
+    for mode in (0, 1):
+        check_against_oracle(m, mode)
+
+
 def test_sqrt_exhaustive_range_on_gpu():
     """dist for every D in [0, 2^22) and random large D, via a 1-row image
     whose only source sits at the left end, so D = j^2 ... plus direct

@@ -232,11 +232,12 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, const short* __res
     const int64_t plane = (int64_t)H * W;
     const int zb = z >> 5, zr = z & 31, zG = zb >> s.gs;
 
-    // z offset of the nearest source along z of every (y, x) of the tile, and
-    // the largest distance among them (columns past the volume's edge count
-    // as 0); the pads hold YNONE.  Each thread first loads the column words
-    // of SU elements, then decodes them, so that SU pairs of loads are in
-    // flight at once.
+    // z offset of the nearest source along z of every (y, x) of the tile, the
+    // largest distance among them and how many exceed DIRECT_MAX_DIST
+    // (columns past the volume's edge count as 0); the pads hold YNONE.  The
+    // offsets come from d16 (copied), or else are decoded from the column
+    // pass's words: each thread first loads the words of SU elements, then
+    // decodes them, so that SU pairs of loads are in flight at once.
     for (int e = tid; e < YPAD * YP; e += nthr) {
         gz[e - YPAD * YP] = YNONE;
         gz[H * YP + e] = YNONE;

@@ -104,10 +104,10 @@ size_t batch_ypass_group_bytes(int H, int lg, int NW) { return ypass_smem(H, lg,
 // z offsets of the nearest source along z of every voxel, written once for
 // the y pass: d16[z][y][x] = z' - z (int16; YNONE when the column has no
 // source).  A thread takes one column of one band of 32 planes: its word and
-// band summary are read once, then the distances to the nearest source at or
-// below each plane (dd, a backward sweep over the word's bits) and at or
-// above it (du, a forward sweep) follow one step each, the nearer taken as
-// the column pass takes it (the one above at a tie).  A y tile staged from
+// band summary are read once, then one sweep over the planes follows the
+// distance to the nearest source at or above each plane step by step and
+// finds the one at or below from the word's remaining bits, the nearer taken
+// as the column pass takes it (the one above at a tie).  A y tile staged from
 // the words would read and decode them once per plane.
 __global__ void __launch_bounds__(256)
 k_zoffsets(int Dz, int64_t cols, ColScratch s, short* __restrict__ d16)
@@ -132,19 +132,16 @@ k_zoffsets(int Dz, int64_t cols, ColScratch s, short* __restrict__ d16)
         return;
     }
     // with a source somewhere in the column, every plane has one above or
-    // below it, closer than BIG
-    int dd[32];
-    int t = dn == (uint32_t)NONE16 ? BIG : (int)dn - (base + 32);
-#pragma unroll
-    for (int r = 31; r >= 0; --r) {
-        t = (w & (1u << r)) ? 0 : t + 1;
-        dd[r] = t;
-    }
-    int nu = up == (uint32_t)NONE16 ? -BIG : (int)up - (base - 1);   // minus the distance above
+    // below it, closer than BIG; the one below comes from the word's bits at
+    // and after the plane (their lowest), else from past the band
+    const int ddout = dn == (uint32_t)NONE16 ? BIG : (int)dn - base;   // from the band's first plane
+    int nu = up == (uint32_t)NONE16 ? -BIG : (int)up - (base - 1);    // minus the distance above
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
         nu = (w & (1u << r)) ? 0 : nu - 1;
-        if (r < rows) out[(int64_t)r * cols] = (short)(dd[r] < -nu ? dd[r] : nu);
+        const uint32_t rest = w >> r;
+        const int dd = rest ? __ffs(rest) - 1 : ddout - r;
+        if (r < rows) out[(int64_t)r * cols] = (short)(dd < -nu ? dd : nu);
     }
 }
 

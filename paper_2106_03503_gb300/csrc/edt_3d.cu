@@ -7,8 +7,8 @@
 //       offset to its nearest source along z;
 //   (y) the lower envelope of Sec. 3.3.1 along y, over f(y') = (z - z')^2 with
 //       z' the nearest source along z in column (y', x): for each voxel it
-//       records the source (z', y') of its owning parabola, packed as
-//       z' << 16 | y' (0xFFFFFFFF = no source in the whole x-slice);
+//       records the source (z', y') of its owning parabola, encoded for
+//       the x pass (offsets and squared length, see xrec_near);
 //   (x) the lower envelope along x over f(x') = (z - z')^2 + (y - y')^2 read
 //       from that record, writing D, F = z'*H*W + y'*W + x' and sqrt(D).
 // The (z', y') record lives in the caller's F (or D) buffer: the x pass reads
@@ -74,9 +74,22 @@ struct LineY {
     }
 };
 
+// y-pass record of a voxel (z, y, x) whose source in its plane x is
+// (z', y', x), written in the form the x pass reads: with dz = z - z', dy =
+// y - y' and dz^2 + dy^2 < 128^2 (so both within +-127), bits 31..24 dz,
+// 23..16 dy (two's complement), 15 clear and 14..0 dz^2 + dy^2, so that a
+// direct search reads a candidate's squared length with one load and a mask;
+// otherwise bit 15 set, z' in bits 31..16 and y' (< 2048) in bits 14..0;
+// PNONE when the plane has no source.  The voxel's own position (dz = dy = 0)
+// is record 0.
+__device__ __forceinline__ uint32_t xrec_near(int dz, int dy, int len2)
+{
+    return ((uint32_t)dz << 24) | (((uint32_t)dy & 0xFFu) << 16) | (uint32_t)len2;
+}
+
 struct OutY {
     uint32_t* P;             // record of voxel (z, y, x0 + lane) at P[y * W]
-    int W;
+    int W, z;
     bool valid;
     __device__ __forceinline__ void finish() const {}
     __device__ __forceinline__ void store(int j0, int cnt, const int* v, const int* f) const
@@ -84,7 +97,11 @@ struct OutY {
         if (!valid) return;
 #pragma unroll
         for (int t = 0; t < OC; ++t)
-            if (t < cnt) P[(int64_t)(j0 + t) * W] = (v[t] == INT32_MAX) ? PNONE : (uint32_t)f[t];
+            if (t < cnt)
+                P[(int64_t)(j0 + t) * W] = v[t] == INT32_MAX ? PNONE
+                                           : v[t] < 128 * 128
+                                               ? xrec_near(z - (int)((uint32_t)f[t] >> 16), j0 + t - (f[t] & 0xFFFF), v[t])
+                                               : (uint32_t)f[t] | 0x8000u;   // f = z' << 16 | y
     }
 };
 
@@ -202,7 +219,8 @@ __device__ bool ydirect(const short* gz, int H, int W, int x0, int z, int64_t pl
             *abort = 1;
             break;
         }
-        if (act) P[(int64_t)z * plane + (int64_t)j * W + x0 + xt] = ((uint32_t)(z + col[bk * YP]) << 16) | (uint32_t)bk;
+        // a result kept has best < rn2 <= 65^2: |z' - z| <= 64 and |y' - y| <= 65
+        if (act) P[(int64_t)z * plane + (int64_t)j * W + x0 + xt] = xrec_near(-col[bk * YP], j - bk, best);
     }
     if (!CHECK) return true;
     sync();
@@ -341,7 +359,7 @@ __device__ void ypass_tile(int H, int W, const ColScratch& s, const short* __res
     else if (2 * far <= entries)
         done = ydirect<true>(gz, H, W, x0, z, plane, P, lane, warp, NW, abort, sync);
     if (!done) {
-        const OutY out{P + (int64_t)z * plane + x0 + lane, W, x0 + lane < W};
+        const OutY out{P + (int64_t)z * plane + x0 + lane, W, z, x0 + lane < W};
         const LineY line{gz, lane, z};
         band_envelope(line, out, sm, H, lg, NW, nullptr, warp, sync);
     }
@@ -360,21 +378,6 @@ k_ypass3d(int H, int W, ColScratch s, const short* __restrict__ d16, int lg, int
 
 // --- x pass ----------------------------------------------------------------
 
-// x-unit record of a voxel (z, y, x) whose y-pass source is (z', y', x):
-// with dz = z - z' and dy = y - y' both within +-127, bits 31..24 dz, 23..16
-// dy (two's complement), 14..0 dz^2 + dy^2 (at most 2 * 127^2 < 2^15) and bit
-// 15 clear, so that a direct search reads a candidate's squared length with
-// one load and a mask; otherwise bit 15 set, z' in bits 31..16 and y' (< 2048)
-// in bits 14..0; PNONE when the plane has no source.  The voxel's own
-// position (dz = dy = 0) is record 0.
-__device__ __forceinline__ uint32_t xrec_encode(uint32_t p, int z, int y)
-{
-    if (p == PNONE) return PNONE;
-    const int dz = z - (int)(p >> 16), dy = y - (int)(p & 0xFFFFu);
-    if (abs(dz) <= 127 && abs(dy) <= 127)
-        return ((uint32_t)(dz & 0xFF) << 24) | ((uint32_t)(dy & 0xFF) << 16) | (uint32_t)(dz * dz + dy * dy);
-    return (p & 0xFFFF0000u) | 0x8000u | (p & 0x7FFFu);
-}
 // the source (z', y') of a record that is not PNONE
 __device__ __forceinline__ void xrec_source(uint32_t q, int z, int y, int& zs, int& ys)
 {
@@ -388,7 +391,7 @@ __device__ __forceinline__ void xrec_source(uint32_t q, int z, int y, int& zs, i
 }
 
 struct LineX {
-    const uint32_t* rec;     // this lane's row of records (xrec_encode)
+    const uint32_t* rec;     // this lane's row of records (xrec_near)
     int z, y, H, W;
     bool valid;
     __device__ __forceinline__ int sq(uint32_t q) const
@@ -454,17 +457,17 @@ size_t batch_xpass_group_bytes(int W, int lg, int NW) { return xpass_smem(W, lg,
 // (Eq. (5) minimised exactly, rightmost x' at a tie, as the hull walk), two
 // steps per test of the stop rule (a step past the stop costs at least its
 // r^2, more than the best, and changes nothing), a candidate's cost being its
-// record's bits 15..0 (xrec_encode).  A warp takes patches of 4 rows x 8 x: a
+// record's bits 15..0 (xrec_near).  A warp takes patches of 4 rows x 8 x: a
 // search runs as far as the farthest lane of its warp, and neighbours in both
 // directions need more alike distances than 32 along x alone.  Without CHECK
-// every record's offsets are within +-64, bits 15..0 are the squared length
-// (at most 2 * 64^2), so a search stops by r = 91 < XPAD and every look past a
-// row's ends reads a pad.  With CHECK (larger offsets, or planes without
-// source) bits 15..0 of an escape record or of PNONE are 32768 or more, below
-// its true cost only when that is 128^2 or more; the searches stop at r = 91,
-// and a search still open there (its best 91^2 or more, so any record whose
-// bits 15..0 are not its true cost could still matter) makes the whole unit
-// give up (returns false; the caller then runs the band engine).
+// every record is one with offsets, its bits 15..0 the squared length and at
+// most 2 * 64^2, so a search stops by r = 91 < XPAD and every look past a
+// row's ends reads a pad.  With CHECK (longer records, escape records or
+// planes without source) bits 15..0 of an escape record or of PNONE are 32768
+// or more, and its true cost 128^2 or more; the searches stop at r = 91, and
+// a search still open there (its best 91^2 or more, so any record whose bits
+// 15..0 are not its true cost could still matter) makes the whole unit give
+// up (returns false; the caller then runs the band engine).
 template <bool CHECK, class Sync>
 __device__ bool xdirect(const uint32_t* rec, int XP, int H, int W, int64_t row0, int64_t nrows, int32_t* D,
                         int32_t* F, float* dist, int lane, int warp, int NW, volatile int* abort, Sync sync)
@@ -532,37 +535,20 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
         const int en = g == 32 ? xrow(31, XP) + W + XPAD : xrow(g, XP);
         for (int a = st + lane; a < en; a += 32) rec[a] = 0xFFFFu;
     }
-    // the rows' (z', y') records, and the largest (z, y) distance among them
-    // (rows past the volume's end count as 0); the (z, y) of RU rows at a time
-    // stepped from the unit's first, so the loads need no divisions, and RU
-    // loads in flight per thread
+    // the rows' records, and the largest squared length among them (bits
+    // 15..0: 32768 or more for an escape record or PNONE; rows past the
+    // volume's end count as 0), RU loads in flight per thread
     constexpr int RU = 4;
     int dmax = 0;
-    int zn = (int)(row0 / H), yn = (int)(row0 % H);
     for (int rl0 = 0; rl0 < 32; rl0 += RU) {
-        int zr[RU], yr[RU];
-#pragma unroll
-        for (int i = 0; i < RU; ++i) {
-            zr[i] = zn;
-            yr[i] = yn;
-            if (++yn == H) {
-                yn = 0;
-                ++zn;
-            }
-        }
         for (int k = tid; k < W; k += nthr) {
             uint32_t p[RU];
 #pragma unroll
             for (int i = 0; i < RU; ++i) p[i] = row0 + rl0 + i < nrows ? P[(row0 + rl0 + i) * W + k] : PNONE;
 #pragma unroll
             for (int i = 0; i < RU; ++i) {
-                uint32_t q = PNONE;
-                if (row0 + rl0 + i < nrows) {
-                    const int dz = zr[i] - (int)(p[i] >> 16), dy = yr[i] - (int)(p[i] & 0xFFFFu);
-                    dmax = max(dmax, p[i] == PNONE ? 32767 : max(abs(dz), abs(dy)));
-                    q = xrec_encode(p[i], zr[i], yr[i]);
-                }
-                rec[xrow(rl0 + i, XP) + k] = q;
+                if (row0 + rl0 + i < nrows) dmax = max(dmax, (int)(p[i] & 0xFFFFu));
+                rec[xrow(rl0 + i, XP) + k] = p[i];
             }
         }
     }
@@ -571,7 +557,7 @@ __device__ void xpass_rows(int Dz, int H, int W, int lg, int NW, const uint32_t*
     sync();
     for (int w = 0; w < NW; ++w) dmax = max(dmax, wmax[w]);
 
-    const bool done = dmax <= DIRECT_MAX_DIST
+    const bool done = dmax <= 2 * DIRECT_MAX_DIST * DIRECT_MAX_DIST
                           ? xdirect<false>(rec, XP, H, W, row0, nrows, D, F, dist, lane, warp, NW, abort, sync)
                           : xdirect<true>(rec, XP, H, W, row0, nrows, D, F, dist, lane, warp, NW, abort, sync);
     if (done) return;

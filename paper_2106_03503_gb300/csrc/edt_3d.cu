@@ -174,27 +174,22 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Direct search of a y tile: each position searches outward along y (Eq.
-// (5) minimised exactly, rightmost y' at a tie, as the hull walk), two steps
-// per test of the stop rule (a step past the stop costs at least its r^2,
-// more than the best, and changes nothing).  A warp takes patches of 4 y x 8
-// x: a search runs as far as the farthest lane of its warp, and neighbours in
-// both directions need more alike distances than 32 along x alone.  Without
-// CHECK every own offset is at most DIRECT_MAX_DIST, so a search stops by
-// r = DIRECT_MAX_DIST + 1 < YPAD and never leaves the padded tile (a pad or a
-// column without source costs 32767^2, more than any answer).  With CHECK
-// (some own offset larger, or a column without source) the searches stop at
-// that distance, and a search still open there makes the whole tile give up
-// (returns false; the caller then runs the band engine, which rewrites every
-// position with the same value).
-template <bool CHECK, class Sync>
-__device__ bool ydirect(const short* gz, int H, int W, int x0, int z, int64_t plane, uint32_t* __restrict__ P,
-                        int lane, int warp, int NW, volatile int* abort, Sync sync)
+// The items of one warp: item (jb, g) is rows 4 jb .. 4 jb + 3 and columns
+// 8 g .. 8 g + 7 of the tile, and the warp takes items warp, warp + NW, ... of
+// the order 4 jb + g.  FIXED (NW a multiple of 4): g is then the same in every
+// item of the warp, so that what depends on it stays out of the loop.
+// Returns false when a search gave up (CHECK).
+template <bool CHECK, bool FIXED>
+__device__ __forceinline__ bool ydirect_items(const short* gz, int H, int W, int x0, int z, int64_t plane,
+                                              uint32_t* __restrict__ P, int lane, int warp, int NW,
+                                              volatile int* abort)
 {
-    const int items = 4 * ((H + 3) >> 2);
-    for (int it = warp; it < items; it += NW) {
-        if (CHECK && __any_sync(FULL, *abort != 0)) break;   // the same decision in every lane
-        const int j = 4 * (it >> 2) + (lane >> 3), xt = 8 * (it & 3) + (lane & 7);
+    const int nyb = (H + 3) >> 2;
+    const int end = FIXED ? nyb : 4 * nyb, step = FIXED ? NW >> 2 : NW;
+    for (int it = FIXED ? warp >> 2 : warp; it < end; it += step) {
+        if (CHECK && __any_sync(FULL, *abort != 0)) return false;   // the same decision in every lane
+        const int jb = FIXED ? it : it >> 2, g = FIXED ? warp & 3 : it & 3;
+        const int j = 4 * jb + (lane >> 3), xt = 8 * g + (lane & 7);
         const bool act = j < H && x0 + xt < W;   // a voxel of the tile
         const short* col = gz + xt;
         int best = 0, bk = j, rn2 = 1;
@@ -217,11 +212,35 @@ __device__ bool ydirect(const short* gz, int H, int W, int x0, int z, int64_t pl
         }
         if (CHECK && __any_sync(FULL, act && rn2 <= best)) {
             *abort = 1;
-            break;
+            return false;
         }
         // a result kept has best < rn2 <= 65^2: |z' - z| <= 64 and |y' - y| <= 65
         if (act) P[(int64_t)z * plane + (int64_t)j * W + x0 + xt] = xrec_near(-col[bk * YP], j - bk, best);
     }
+    return true;
+}
+
+// Direct search of a y tile: each position searches outward along y (Eq.
+// (5) minimised exactly, rightmost y' at a tie, as the hull walk), two steps
+// per test of the stop rule (a step past the stop costs at least its r^2,
+// more than the best, and changes nothing).  A warp takes patches of 4 y x 8
+// x: a search runs as far as the farthest lane of its warp, and neighbours in
+// both directions need more alike distances than 32 along x alone.  Without
+// CHECK every own offset is at most DIRECT_MAX_DIST, so a search stops by
+// r = DIRECT_MAX_DIST + 1 < YPAD and never leaves the padded tile (a pad or a
+// column without source costs 32767^2, more than any answer).  With CHECK
+// (some own offset larger, or a column without source) the searches stop at
+// that distance, and a search still open there makes the whole tile give up
+// (returns false; the caller then runs the band engine, which rewrites every
+// position with the same value).
+template <bool CHECK, class Sync>
+__device__ bool ydirect(const short* gz, int H, int W, int x0, int z, int64_t plane, uint32_t* __restrict__ P,
+                        int lane, int warp, int NW, volatile int* abort, Sync sync)
+{
+    if ((NW & 3) == 0)
+        ydirect_items<CHECK, true>(gz, H, W, x0, z, plane, P, lane, warp, NW, abort);
+    else
+        ydirect_items<CHECK, false>(gz, H, W, x0, z, plane, P, lane, warp, NW, abort);
     if (!CHECK) return true;
     sync();
     return *abort == 0;
@@ -453,29 +472,22 @@ __host__ __device__ static inline size_t xpass_smem(int W, int lg, int NW)
 
 size_t batch_xpass_group_bytes(int W, int lg, int NW) { return xpass_smem(W, lg, NW); }
 
-// Direct search of an x unit: each position searches outward along its row
-// (Eq. (5) minimised exactly, rightmost x' at a tie, as the hull walk), two
-// steps per test of the stop rule (a step past the stop costs at least its
-// r^2, more than the best, and changes nothing), a candidate's cost being its
-// record's bits 15..0 (xrec_near).  A warp takes patches of 4 rows x 8 x: a
-// search runs as far as the farthest lane of its warp, and neighbours in both
-// directions need more alike distances than 32 along x alone.  Without CHECK
-// every record is one with offsets, its bits 15..0 the squared length and at
-// most 2 * 64^2, so a search stops by r = 91 < XPAD and every look past a
-// row's ends reads a pad.  With CHECK (longer records, escape records or
-// planes without source) bits 15..0 of an escape record or of PNONE are 32768
-// or more, and its true cost 128^2 or more; the searches stop at r = 91, and
-// a search still open there (its best 91^2 or more, so any record whose bits
-// 15..0 are not its true cost could still matter) makes the whole unit give
-// up (returns false; the caller then runs the band engine).
-template <bool CHECK, class Sync>
-__device__ bool xdirect(const uint32_t* rec, int XP, int H, int W, int64_t row0, int64_t nrows, int32_t* D,
-                        int32_t* F, float* dist, int lane, int warp, int NW, volatile int* abort, Sync sync)
+// The items of one warp: item (jb, g) is rows 4 g .. 4 g + 3 of the unit and
+// columns 8 jb .. 8 jb + 7, and the warp takes items warp, warp + NW, ... of
+// the order 8 jb + g.  FIXED (NW a multiple of 8): g is then the same in
+// every item of the warp, so that the rows' pointers and output offsets stay
+// out of the loop.  Returns false when a search gave up (CHECK).
+template <bool CHECK, bool FIXED>
+__device__ __forceinline__ bool xdirect_items(const uint32_t* rec, int XP, int H, int W, int64_t row0,
+                                              int64_t nrows, int32_t* D, int32_t* F, float* dist, int lane,
+                                              int warp, int NW, volatile int* abort)
 {
-    const int items = 8 * ((W + 7) >> 3);
-    for (int it = warp; it < items; it += NW) {
-        if (CHECK && __any_sync(FULL, *abort != 0)) break;   // the same decision in every lane
-        const int rl = 4 * (it & 7) + (lane >> 3), j = 8 * (it >> 3) + (lane & 7);
+    const int nj = (W + 7) >> 3;
+    const int end = FIXED ? nj : 8 * nj, step = FIXED ? NW >> 3 : NW;
+    for (int it = FIXED ? warp >> 3 : warp; it < end; it += step) {
+        if (CHECK && __any_sync(FULL, *abort != 0)) return false;   // the same decision in every lane
+        const int jb = FIXED ? it : it >> 3, g = FIXED ? warp & 7 : it & 7;
+        const int rl = 4 * g + (lane >> 3), j = 8 * jb + (lane & 7);
         const int64_t row = row0 + rl;
         const bool act = row < nrows && j < W;
         const uint32_t* rr = rec + xrow(rl, XP);
@@ -497,17 +509,46 @@ __device__ bool xdirect(const uint32_t* rec, int XP, int H, int W, int64_t row0,
         }
         if (CHECK && __any_sync(FULL, act && rn2 <= best)) {
             *abort = 1;
-            break;
+            return false;
         }
         if (act) {
             const uint32_t p = rr[bk];
             const int dz = (int)(int8_t)(p >> 24), dy = (int)(int8_t)((p >> 16) & 0xFFu);
-            const int64_t q = row * W + j;
+            // row = z * H + y; every term below 2^31 (the volume has fewer
+            // voxels, and |dz| < Dz, |dy| < H)
+            const int rowW = (int)(row * W);
+            const int64_t q = (int64_t)rowW + j;
             if (D) D[q] = best;
-            if (F) F[q] = (int)((row - (int64_t)dz * H - dy) * W + bk);   // row = z * H + y
+            if (F) F[q] = rowW + bk - (dz * H + dy) * W;
             if (dist) dist[q] = sqrt_rn_int(best);
         }
     }
+    return true;
+}
+
+// Direct search of an x unit: each position searches outward along its row
+// (Eq. (5) minimised exactly, rightmost x' at a tie, as the hull walk), two
+// steps per test of the stop rule (a step past the stop costs at least its
+// r^2, more than the best, and changes nothing), a candidate's cost being its
+// record's bits 15..0 (xrec_near).  A warp takes patches of 4 rows x 8 x: a
+// search runs as far as the farthest lane of its warp, and neighbours in both
+// directions need more alike distances than 32 along x alone.  Without CHECK
+// every record is one with offsets, its bits 15..0 the squared length and at
+// most 2 * 64^2, so a search stops by r = 91 < XPAD and every look past a
+// row's ends reads a pad.  With CHECK (longer records, escape records or
+// planes without source) bits 15..0 of an escape record or of PNONE are 32768
+// or more, and its true cost 128^2 or more; the searches stop at r = 91, and
+// a search still open there (its best 91^2 or more, so any record whose bits
+// 15..0 are not its true cost could still matter) makes the whole unit give
+// up (returns false; the caller then runs the band engine).
+template <bool CHECK, class Sync>
+__device__ bool xdirect(const uint32_t* rec, int XP, int H, int W, int64_t row0, int64_t nrows, int32_t* D,
+                        int32_t* F, float* dist, int lane, int warp, int NW, volatile int* abort, Sync sync)
+{
+    if ((NW & 7) == 0)
+        xdirect_items<CHECK, true>(rec, XP, H, W, row0, nrows, D, F, dist, lane, warp, NW, abort);
+    else
+        xdirect_items<CHECK, false>(rec, XP, H, W, row0, nrows, D, F, dist, lane, warp, NW, abort);
     if (!CHECK) return true;
     sync();
     return *abort == 0;

@@ -492,19 +492,23 @@ __device__ __forceinline__ bool xdirect_items(const uint32_t* rec, int XP, int H
         const bool act = row < nrows && j < W;
         const uint32_t* rr = rec + xrow(rl, XP);
         int best = 0, bk = j, rn2 = 1;
+        const uint16_t* c16 = reinterpret_cast<const uint16_t*>(rr);   // bits 15..0 of record k at c16[2 k]
         if (act) {
-            best = (int)(rr[j] & 0xFFFFu);
+            // one key per candidate k, cost * 256 + 128 - (k - j) (costs
+            // below 2^17, |k - j| <= 91): the least key has the least cost
+            // and, at a tie, the rightmost k; a step's four keys fold in a
+            // tree of minimums
+            int key = ((int)c16[2 * j] << 8) + 128;
             int r = 1, r2 = 1;
-            for (; r2 <= best && (!CHECK || r < 90); r += 2, r2 += 4 * r - 4) {
-                const int r2b = r2 + 2 * r + 1;
-                const int cl = (int)(rr[j - r] & 0xFFFFu) + r2, cr = (int)(rr[j + r] & 0xFFFFu) + r2;
-                const int cl2 = (int)(rr[j - r - 1] & 0xFFFFu) + r2b;
-                const int cr2 = (int)(rr[j + r + 1] & 0xFFFFu) + r2b;
-                if (cl < best) { best = cl; bk = j - r; }
-                if (cr <= best) { best = cr; bk = j + r; }
-                if (cl2 < best) { best = cl2; bk = j - r - 1; }
-                if (cr2 <= best) { best = cr2; bk = j + r + 1; }
+            for (; r2 <= (key >> 8) && (!CHECK || r < 90); r += 2, r2 += 4 * r - 4) {
+                const int t = (r2 << 8) + 128, t2 = t + ((2 * r + 1) << 8);
+                const int kl = ((int)c16[2 * (j - r)] << 8) + t + r, kr = ((int)c16[2 * (j + r)] << 8) + t - r;
+                const int kl2 = ((int)c16[2 * (j - r - 1)] << 8) + t2 + r + 1;
+                const int kr2 = ((int)c16[2 * (j + r + 1)] << 8) + t2 - r - 1;
+                key = min(key, min(min(kl, kr), min(kl2, kr2)));
             }
+            best = key >> 8;
+            bk = j + 128 - (key & 0xFF);
             rn2 = r2;   // r^2 of the nearest distance not searched
         }
         if (CHECK && __any_sync(FULL, act && rn2 <= best)) {

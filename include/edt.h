@@ -185,9 +185,10 @@ edt_status edt_batch(edt_plan *plan, const edt_job *jobs, int n,
  * 2^8, 2^7 or 2^6 columns; 3-D jobs: 64, 32 or 128 positions per warp for the
  * y pass, then 32, 64 or 128 for the x pass -- and keeps the fastest in the
  * process-wide table that every later batch uses (saved and loaded with
- * edt_tune_save / edt_tune_load), provided the whole batch then runs faster
- * than with the built-in geometry (else the built-in geometry is stored for
- * those classes).  Rows wider than 2048 have no knob.  n must not exceed the
+ * edt_tune_save / edt_tune_load), provided the whole batch then runs more
+ * than 1 % faster than with the built-in geometry (the two timed alternately,
+ * twice each, the better time of each compared; else the built-in geometry is
+ * stored for those classes).  Rows wider than 2048 have no knob.  n must not exceed the
  * plan's n_max (EDT_ERR_INVALID).  Runs the jobs (device pointers, as
  * edt_batch) several times on `stream`, which overwrites their outputs with
  * the same bits; synchronous.  Results never depend on the choice. */

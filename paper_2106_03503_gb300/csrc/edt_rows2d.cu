@@ -236,6 +236,104 @@ __device__ bool rows2d_direct(const uint32_t* sbits, const uint32_t* supdn, int 
     return *abort == 0;
 }
 
+// Direct row pass of band b on 4 x 8 patches (the batch's bands): the same
+// exact search as rows2d_direct, but each warp takes 4 rows of the band at a
+// time and its lanes a patch of 4 rows x 8 consecutive columns, so that the
+// lanes of a warp, whose searches run as long as the farthest one, hold
+// nearer distances than 32 columns of one row do.  The 4 rows' vertical
+// offsets are int8: PATCH_NONE (-128) for a column without source, the
+// others clamped to +-127.  A clamped or missing value costs at least 127^2,
+// and never more than the true cost, so a search whose best is below 127^2
+// chose an exact value and no clamped one could beat it; a best of 127^2 or
+// more gives up (as a search still open at DIRECT_ROW_CAP does).  Warp w's
+// buffer is 4 rows of patch_pitch(W) bytes at buf + 4 w patch_pitch(W), each
+// with DPAD bytes of pad (PATCH_NONE) before column 0 and after column W - 1;
+// the pitch is 32 mod 128 bytes, so the 4 rows of a patch fall on disjoint
+// banks.  Called and returning as rows2d_direct (all of the band's rows).
+constexpr int PATCH_NONE = -128;
+__host__ __device__ inline int patch_pitch(int W) { return ((W + 2 * DPAD + 127) & ~127) + 32; }
+__host__ __device__ inline size_t patch_buf_bytes(int W, int NW)
+{
+    return W <= DIRECT_ROW_W ? (size_t)NW * 4 * patch_pitch(W) : 0;
+}
+
+template <class Sync>
+__device__ bool rows2d_direct_patches(const uint32_t* sbits, const uint32_t* supdn, int b, int H, int W,
+                                      int32_t* D, int32_t* F, float* dist, int8_t* buf, volatile int* abort,
+                                      int lane, int warp, int NW, Sync sync)
+{
+    const int base = b * 32, rows = min(32, H - base), P = patch_pitch(W);
+    int8_t* qb = buf + (size_t)warp * 4 * P + DPAD;   // row 0, column 0 of this warp's 4 rows
+    for (int t = lane; t < 4 * DPAD; t += 32) {        // the pads: no source beyond the rows' ends
+        const int rr = t / DPAD, e = t - rr * DPAD;
+        qb[rr * P - 1 - e] = (int8_t)PATCH_NONE;
+        qb[rr * P + W + e] = (int8_t)PATCH_NONE;
+    }
+    const int nq = (rows + 3) >> 2, nj = (W + 7) >> 3;
+    const int8_t* rb = qb + (lane >> 3) * P;            // this lane's row of a patch
+    for (int q = warp; q < nq; q += NW) {
+        if (__any_sync(FULL, *abort != 0)) break;      // the same decision in every lane
+        for (int rr = 0; rr < 4 && 4 * q + rr < rows; ++rr) {
+            const int r = 4 * q + rr, i = base + r;
+            const uint32_t mle = FULL >> (31 - r), mge = FULL << r;
+            for (int k = lane; k < W; k += 32) {
+                const uint32_t w = sbits[k], ud = supdn[k];
+                const uint32_t a = w & mle, bb = w & mge;
+                const int up = a ? base + 31 - __clz(a) : (int)(short)(ud & 0xFFFFu);
+                const int dn = bb ? base + __ffs(bb) - 1 : (int)(ud >> 16);
+                const int du = i - up, dd = dn - i;
+                const int o = min(du, dd) >= 32768 ? PATCH_NONE : max(-127, min(127, du <= dd ? up - i : dn - i));
+                qb[rr * P + k] = (int8_t)o;
+            }
+        }
+        __syncwarp();
+        const int r = 4 * q + (lane >> 3), i = base + r;
+        bool gave_up = false;
+        for (int jb = 0; jb < nj; ++jb) {
+            const int j = 8 * jb + (lane & 7);
+            bool unsettled = false;
+            if (r < rows && j < W) {
+                // two steps per test of the stop rule; the pads make bounds
+                // tests unneeded
+                const int o = rb[j];
+                int best = o * o, bk = j;
+                int rr = 1;
+                for (int r2 = 1; rr <= DIRECT_ROW_CAP && r2 <= best; rr += 2, r2 += 4 * rr - 4) {
+                    const int r2b = r2 + 2 * rr + 1;
+                    const int ol = rb[j - rr], orr = rb[j + rr];
+                    const int ol2 = rb[j - rr - 1], orr2 = rb[j + rr + 1];
+                    const int cl = ol * ol + r2, cr = orr * orr + r2;
+                    const int cl2 = ol2 * ol2 + r2b, cr2 = orr2 * orr2 + r2b;
+                    if (cl < best) { best = cl; bk = j - rr; }
+                    if (cr <= best) { best = cr; bk = j + rr; }
+                    if (cl2 < best) { best = cl2; bk = j - rr - 1; }
+                    if (cr2 <= best) { best = cr2; bk = j + rr + 1; }
+                }
+                // rr: the nearest distance not searched
+                unsettled = best >= 127 * 127 || (rr * rr <= best && (j - rr >= 0 || j + rr < W));
+                if (!unsettled) {
+                    const int ob = rb[bk];   // exact: |ob| <= 126
+                    const int64_t qq = (int64_t)i * W + j;
+                    if (D) D[qq] = best;
+                    if (F) F[qq] = (i + ob) * W + bk;
+                    if (dist) dist[qq] = sqrt_rn_int(best);
+                }
+            }
+            if (__any_sync(FULL, unsettled)) {
+                gave_up = true;
+                break;
+            }
+        }
+        __syncwarp();
+        if (gave_up) {
+            *abort = 1;
+            break;
+        }
+    }
+    sync();
+    return *abort == 0;
+}
+
 // Tensor maps for TMA row stores: the output viewed as [rows][W] with an
 // 8 x 32 box (8 columns, 32 rows).  Needs W % 4 == 0 (16-byte row pitch) and a
 // 16-byte aligned base.
@@ -444,9 +542,13 @@ void batch_row_geometry(int W, int lgmin, int& lg, int& NW, int& groups)
     groups = BATCH_K2_WARPS / NW;
 }
 
+// A batch band's shared memory: its column data, then the band engine, whose
+// memory the direct search's patch buffers use first (the engine runs after
+// the search, past a barrier, only on a band the search gave up).
 __host__ __device__ static size_t batch_group_bytes(int W, int lg, int NW)
 {
-    return band2d_col_bytes(W) + band_smem_bytes(NW, (1 << lg) >> 5) + direct_row_bytes(W, NW);
+    const size_t eng = band_smem_bytes(NW, (1 << lg) >> 5), pb = patch_buf_bytes(W, NW);
+    return band2d_col_bytes(W) + (eng > pb ? eng : pb);
 }
 
 // Segment minimums the autotuner may choose for the rows2d phase (the
@@ -513,11 +615,9 @@ k_batch_rows2d(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__
             stage_band(J.s, b, H, W, sbits, supdn, sfull, wg * 32 + lane, NW * 32);
             sync();
             bool done = false;
-            if (W <= DIRECT_ROW_W) {
-                short* rowbuf = direct_rowbuf(reinterpret_cast<unsigned char*>(sm.ctr) + 16, wg, W);
-                done = rows2d_direct(sbits, supdn, b, H, W, J.D, J.F, J.dist, rowbuf, &s_abort[grp], lane, wg, NW,
-                                     sync);
-            }
+            if (W <= DIRECT_ROW_W)
+                done = rows2d_direct_patches(sbits, supdn, b, H, W, J.D, J.F, J.dist,
+                                             reinterpret_cast<int8_t*>(sm.hb), &s_abort[grp], lane, wg, NW, sync);
             BandRow2D line;
             line.bits = sbits;
             line.updn = supdn;

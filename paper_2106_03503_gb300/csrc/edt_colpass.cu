@@ -89,14 +89,16 @@ __device__ __forceinline__ uint32_t nz_bits16(uint4 a)
            (nz_bits4(a.w) << 12);
 }
 
-// Source bits of the 32 bytes at p (only the first ncols are valid).  VEC:
-// p is 16-byte aligned.  al: bit 0 = the mask starts on a 4-byte boundary,
-// bit 1 = on a 16-byte boundary, so the aligned word / 16-byte chunk holding
-// byte p (and the bytes before p in it) lies inside the mask; end = one past
-// the mask's last byte.  Aligned 16-byte loads of the window read each byte
-// once and carry the evict-first hint.  An unaligned window is read as the
-// two or three aligned 16-byte chunks that cover it while they end inside
-// the mask (else as aligned words plus its last bytes one by one); the
+// Source bits of the 32 bytes at p (only the first ncols are valid: the
+// others may hold the bits of the bytes that follow, which the caller masks
+// off).  VEC: p is 16-byte aligned.  al: bit 0 = the mask starts on a 4-byte
+// boundary, bit 1 = on a 16-byte boundary, so the aligned word / 16-byte
+// chunk holding byte p (and the bytes before p in it) lies inside the mask;
+// end = one past the mask's last byte.  Aligned 16-byte loads of the window
+// read each byte once and carry the evict-first hint.  An unaligned window,
+// or one of fewer than 32 columns (a row's last tile), is read as the two or
+// three aligned 16-byte chunks that cover 32 bytes from p while they end
+// inside the mask (else as aligned words plus its last bytes one by one); the
 // chunks that straddle two tiles are read by both, so these loads keep the
 // default caching.
 template <bool VEC>
@@ -112,7 +114,7 @@ __device__ __forceinline__ uint32_t load_row_bits(const uint8_t* __restrict__ p,
         const uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
         return nz_bits16(a);
     }
-    if (!VEC && (al & 2) && ncols == 32) {
+    if (!VEC && (al & 2)) {
         const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(15);
         const int o = (int)(reinterpret_cast<uintptr_t>(p) & 15);
         if (a + (o ? 48 : 32) <= reinterpret_cast<uintptr_t>(end)) {

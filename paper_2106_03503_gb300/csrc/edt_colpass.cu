@@ -258,11 +258,7 @@ __device__ __forceinline__ void link_groups(const ColGeom& g, const ColScratch& 
 // view's column v at row r is the image's column v + r - (imgH - 1) (SHEAR
 // +1: the diagonals j - i = const become columns) or v - r (SHEAR -1: the
 // anti-diagonals); pixels outside the image are no sources.
-//
-// BALLOT: transpose with 32 ballots instead of the shuffle butterfly (five
-// dependent shuffles); measured faster in the persistent batch kernel, where
-// each warp walks many small tiles one after the other.
-template <bool VEC, bool PAIR, int SHEAR = 0, bool BALLOT = false>
+template <bool VEC, bool PAIR, int SHEAR = 0>
 __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g, int mode,
                              const ColScratch& s, const ColScratch& s1, int64_t tile, int G,
                              uint32_t (*cw)[32], uint32_t (*upS)[32], int imgH = 0, int64_t imgW = 0)
@@ -304,16 +300,7 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (bl + u >= nbg) break;
-            uint32_t mine = 0;
-            if (BALLOT) {
-#pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                    const uint32_t b = __ballot_sync(FULL, (src[u] >> t) & 1u);
-                    if (lane == t) mine = b;
-                }
-            } else {
-                mine = transpose32(src[u], lane);
-            }
+            const uint32_t mine = transpose32(src[u], lane);
             cw[bl + u][lane] = mine;
             if (col < W) s.C[(int64_t)(b0 + bl + u) * W + col] = mine;
         }
@@ -424,11 +411,11 @@ k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
         const ColScratch s = J.s;
         const int64_t local = gw - J.k_first[PH_COL];
         if (J.vec)
-            colbits_warp<true, false, 0, true>(J.mask, g, J.mode, s, s, local % g.ntiles,
-                                               (int)(local / g.ntiles), cw[warp], upS[warp]);
+            colbits_warp<true, false>(J.mask, g, J.mode, s, s, local % g.ntiles, (int)(local / g.ntiles),
+                                      cw[warp], upS[warp]);
         else
-            colbits_warp<false, false, 0, true>(J.mask, g, J.mode, s, s, local % g.ntiles,
-                                                (int)(local / g.ntiles), cw[warp], upS[warp]);
+            colbits_warp<false, false>(J.mask, g, J.mode, s, s, local % g.ntiles, (int)(local / g.ntiles),
+                                       cw[warp], upS[warp]);
         __syncwarp();
     }
 }

@@ -313,7 +313,16 @@ __device__ void colbits_warp(const uint8_t* __restrict__ mask, const ColGeom& g,
         if (PAIR) group_scan(g, s1, cw, upS, true, G, col);
     }
 
-    // (3) the last group of this tile to finish links the groups
+    // (3) the last group of this tile to finish links the groups; a column
+    // of one group has nothing above or below it to link
+    if (g.nG == 1) {
+        if (col < W) {
+            const uint32_t none = (uint32_t)NONE16 | ((uint32_t)NONE16 << 16);
+            s.GAB[col] = none;
+            if (PAIR) s1.GAB[col] = none;
+        }
+        return;
+    }
     __threadfence();
     __syncwarp();
     unsigned old = 0;

@@ -213,3 +213,39 @@ def test_full_batch_workload_4096():
         assert np.array_equal(D, Do), k
         assert feature_valid_fast(masks_np[k], 0, D, F) is None
         assert np.array_equal(F, Fo), k
+
+
+def test_batch_patch_search_clamp_and_ragged_patches():
+    """The batch's row search on 4 x 8 patches keeps vertical offsets as int8,
+    clamped at +-127: a single source in a narrow image puts offsets of 126
+    (kept exact: with the source in row 1, the band of rows 96..127 settles),
+    127 and 128 and beyond (a best of 127^2 or more: the band falls back to
+    the hull) in the same columns; heights that are not a multiple of 4 and widths
+    that are not a multiple of 8 leave partial patches; widths 1024 and 1025
+    sit on both sides of the direct search's limit."""
+    import torch
+    from paper_2106_03503_gb300 import edt
+    masks = []
+    for (H, W, i, j) in [(300, 20, 0, 5), (300, 20, 1, 5), (300, 20, 299, 19), (260, 70, 130, 35), (129, 9, 0, 0)]:
+        m = np.zeros((H, W), np.uint8)
+        m[i, j] = 1
+        masks.append(m)
+    rng = np.random.default_rng(31)
+    for H in (1, 2, 3, 5, 6, 7, 33, 35):
+        for W in (1, 7, 9, 15, 17, 33):
+            masks.append(inputs.bernoulli_mask((H, W), float(rng.choice([0.05, 0.3])), 3100 + 37 * H + W))
+    for W in (1016, 1023, 1024, 1025):
+        masks.append(inputs.bernoulli_mask((70, W), 0.002, 3300 + W))
+    jobs, refs = [], []
+    for k, m_np in enumerate(masks):
+        m = torch.from_numpy(m_np).cuda()
+        mode = k % 2 if k >= 5 else 0
+        D = torch.full(m.shape, -5, dtype=torch.int32, device="cuda")
+        F = torch.full(m.shape, -5, dtype=torch.int32, device="cuda")
+        dist = torch.full(m.shape, -5.0, dtype=torch.float32, device="cuda")
+        jobs.append((m, mode, D, F, dist))
+        refs.append(edt.feature(m, mode, want_dist=True))
+    plan = edt.Plan(len(jobs), sum(m.size for m in masks))
+    plan.run(jobs)
+    _check(jobs, refs, torch)
+    plan.close()

@@ -258,3 +258,17 @@ def test_mask_alignments(shape, offset):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(D.cpu().numpy(), oracle.edt(m_np, mode)[0])
         assert feature_valid_fast(m_np, mode, D.cpu().numpy(), F.cpu().numpy()) is None
+
+
+def test_3d_record_forms():
+    """A source line along x at (z, y) = (0, 0): every x plane's records have
+    squared lengths on both sides of 128^2 (offset form below it, the source's
+    own coordinates above it, whose true cost the hull then reads), and with
+    the line broken every seventh plane's records are "no source"."""
+    m = np.zeros((150, 150, 24), np.uint8)
+    m[0, 0, :] = 1
+    check_against_oracle(m, 0)
+    m = np.zeros((150, 150, 24), np.uint8)
+    m[0, 0, ::7] = 1
+    for mode in (0, 1):
+        check_against_oracle(m, mode)

@@ -245,13 +245,18 @@ __device__ bool rows2d_direct(const uint32_t* sbits, const uint32_t* supdn, int 
 // others clamped to +-127.  A clamped or missing value costs at least 127^2,
 // and never more than the true cost, so a search whose best is below 127^2
 // chose an exact value and no clamped one could beat it; a best of 127^2 or
-// more gives up (as a search still open at DIRECT_ROW_CAP does).  Warp w's
+// more gives up (as a search still open at PATCH_ROW_CAP does).  Warp w's
 // buffer is 4 rows of patch_pitch(W) bytes at buf + 4 w patch_pitch(W), each
-// with DPAD bytes of pad (PATCH_NONE) before column 0 and after column W - 1;
+// with PPAD bytes of pad (PATCH_NONE) before column 0 and after column W - 1;
 // the pitch is 32 mod 128 bytes, so the 4 rows of a patch fall on disjoint
 // banks.  Called and returning as rows2d_direct (all of the band's rows).
+// The patch search stops at PATCH_ROW_CAP columns, further than the row-wise
+// search: a patch's lanes hold more alike distances, so searching on costs
+// less than handing the band to the hull engine.
 constexpr int PATCH_NONE = -128;
-__host__ __device__ inline int patch_pitch(int W) { return ((W + 2 * DPAD + 127) & ~127) + 32; }
+constexpr int PATCH_ROW_CAP = 48;
+constexpr int PPAD = PATCH_ROW_CAP + 2;
+__host__ __device__ inline int patch_pitch(int W) { return ((W + 2 * PPAD + 127) & ~127) + 32; }
 __host__ __device__ inline size_t patch_buf_bytes(int W, int NW)
 {
     return W <= DIRECT_ROW_W ? (size_t)NW * 4 * patch_pitch(W) : 0;
@@ -263,9 +268,9 @@ __device__ bool rows2d_direct_patches(const uint32_t* sbits, const uint32_t* sup
                                       int lane, int warp, int NW, Sync sync)
 {
     const int base = b * 32, rows = min(32, H - base), P = patch_pitch(W);
-    int8_t* qb = buf + (size_t)warp * 4 * P + DPAD;   // row 0, column 0 of this warp's 4 rows
-    for (int t = lane; t < 4 * DPAD; t += 32) {        // the pads: no source beyond the rows' ends
-        const int rr = t / DPAD, e = t - rr * DPAD;
+    int8_t* qb = buf + (size_t)warp * 4 * P + PPAD;   // row 0, column 0 of this warp's 4 rows
+    for (int t = lane; t < 4 * PPAD; t += 32) {        // the pads: no source beyond the rows' ends
+        const int rr = t / PPAD, e = t - rr * PPAD;
         qb[rr * P - 1 - e] = (int8_t)PATCH_NONE;
         qb[rr * P + W + e] = (int8_t)PATCH_NONE;
     }
@@ -298,7 +303,7 @@ __device__ bool rows2d_direct_patches(const uint32_t* sbits, const uint32_t* sup
                 const int o = rb[j];
                 int best = o * o, bk = j;
                 int rr = 1;
-                for (int r2 = 1; rr <= DIRECT_ROW_CAP && r2 <= best; rr += 2, r2 += 4 * rr - 4) {
+                for (int r2 = 1; rr <= PATCH_ROW_CAP && r2 <= best; rr += 2, r2 += 4 * rr - 4) {
                     const int r2b = r2 + 2 * rr + 1;
                     const int ol = rb[j - rr], orr = rb[j + rr];
                     const int ol2 = rb[j - rr - 1], orr2 = rb[j + rr + 1];

@@ -96,12 +96,16 @@ struct OutY {
     {
         if (!valid) return;
 #pragma unroll
-        for (int t = 0; t < OC; ++t)
-            if (t < cnt)
-                P[(int64_t)(j0 + t) * W] = v[t] == INT32_MAX ? PNONE
-                                           : v[t] < 128 * 128
-                                               ? xrec_near(z - (int)((uint32_t)f[t] >> 16), j0 + t - (f[t] & 0xFFFF), v[t])
-                                               : (uint32_t)f[t] | 0x8000u;   // f = z' << 16 | y
+        for (int t = 0; t < OC; ++t) {
+            if (t >= cnt) continue;
+            const uint32_t src = (uint32_t)f[t];   // z' << 16 | y'
+            uint32_t q = PNONE;
+            if (v[t] < 128 * 128)
+                q = xrec_near(z - (int)(src >> 16), j0 + t - (int)(src & 0xFFFFu), v[t]);
+            else if (v[t] != INT32_MAX)
+                q = src | 0x8000u;
+            P[(int64_t)(j0 + t) * W] = q;
+        }
     }
 };
 

@@ -12,9 +12,10 @@
 // the squared vertical distance D_v(k) = (i - g)^2 of Fig. 18(b) is rebuilt on
 // demand and never stored; all 32 rows read the same column word at once.
 // Bands of rows up to DIRECT_ROW_W wide first try an exact direct search
-// (rows2d_direct: lanes on 32 consecutive columns of one row); a band in
-// which some search runs past DIRECT_ROW_CAP columns falls back to the band
-// engine, which gives the same bits.
+// (rows2d_direct: lanes on 32 consecutive columns of one row, giving up past
+// DIRECT_ROW_CAP columns; in the batch rows2d_direct_patches: lanes on 4 rows
+// x 8 columns, giving up past PATCH_ROW_CAP); a band in which some search
+// gives up falls back to the band engine, which gives the same bits.
 #include "edt_engine.cuh"
 #include "edt_internal.h"
 

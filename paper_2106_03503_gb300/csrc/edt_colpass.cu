@@ -391,8 +391,8 @@ cudaError_t launch_colbits_sheared(const uint8_t* mask, const ColGeom& g, int mo
 
 // Persistent column pass over every job of a batch (for a 3-D job the z pass
 // over its Dz x H*W view): warp units are numbered job by job
-// (k_first[PH_COL]); warp w takes units w, w + (warps of the grid), ...: it
-// finds its first job by binary search once and then steps from job to job.
+// (k_first[PH_COL]); warp w takes units w, w + (warps of the grid), ...,
+// finding each unit's job by binary search from the previous one's.
 __global__ void __launch_bounds__(K1_WARPS * 32)
 k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict__ jobs)
 {
@@ -414,7 +414,16 @@ k_batch_colbits(const BatchHeader* __restrict__ hdr, const BatchJob* __restrict_
         }
     }
     for (int64_t gw = w; gw < total; gw += nw) {
-        while (lo + 1 < nj && jobs[lo + 1].k_first[PH_COL] <= gw) ++lo;
+        // the unit's job: a step of nw units can pass many jobs, so a binary
+        // search over the jobs after lo (each probe reads another job's entry)
+        if (lo + 1 < nj && jobs[lo + 1].k_first[PH_COL] <= gw) {
+            int a = lo + 1, b = nj - 1;
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (jobs[mid].k_first[PH_COL] <= gw) a = mid; else b = mid - 1;
+            }
+            lo = a;
+        }
         const BatchJob& J = jobs[lo];
         const ColGeom g = J.g;
         const ColScratch s = J.s;

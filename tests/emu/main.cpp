@@ -198,6 +198,24 @@ static int run_batch(int njobs, int blocks)
         j.D = alloc_words(j.n);
         j.F = alloc_words(j.n);
     }
+    // two 300 x 20 images with one source each (row 0, then row 1; column 5):
+    // vertical offsets of 126, 127 and beyond in the same columns, on both
+    // sides of the batch row search's int8 clamp
+    for (int srow = 0; srow < 2; ++srow) {
+        Job j;
+        j.ndim = 2;
+        j.shape[0] = 300;
+        j.shape[1] = 20;
+        j.shape[2] = 0;
+        j.mode = 0;
+        j.n = 300 * 20;
+        j.mask.assign(j.n, 0);
+        j.mask[(size_t)srow * 20 + 5] = 1;
+        j.D = alloc_words(j.n);
+        j.F = alloc_words(j.n);
+        js.push_back(std::move(j));
+    }
+    njobs = (int)js.size();
     std::vector<edt_job> ej(njobs);
     for (int k = 0; k < njobs; ++k) {
         Job& j = js[k];
